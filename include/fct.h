@@ -1,0 +1,200 @@
+/*
+ * fct.h -- C ABI of the GB300 sparse Fast Chebyshev Transform hot path.
+ *
+ * Method (Jones, Letourneau, Morse, Langston, "A Sparse Fast Chebyshev
+ * Transform for High-Dimensional Approximation"):
+ *   given a known multi-index support S (N columns) and an L-grid of K tensor
+ *   Chebyshev grids (Sec. 3.2, Algorithm 1), sample f on every grid, take each
+ *   grid's multi-dimensional DCT (Algorithm 3), and solve
+ *     c* = argmin_c || F f - A c ||_2                       (Sec. 3.4)
+ *   where A stacks one alias block per grid (Eq. (L-grid_A_mat)) whose
+ *   entries come from the Chebyshev aliasing relation (Lemma (lem:aliasing),
+ *   Eq. (aliasing_matrix_nd_diff)), by the CG method on the least-squares
+ *   problem (CGLS).
+ *
+ * Grid and DCT kind implemented here: Chebyshev extrema points
+ * x_j = cos(pi j/(n-1)), j = 0..n-1, with an interpolating DCT-I per axis, so
+ * that degree m folds to fold_n(m) = r <= n-1 ? r : 2(n-1)-r, r = m mod 2(n-1).
+ * An axis with n == 1 holds one sample at a caller-given node xi; a column's
+ * entry on such a grid is prod_{i: n_i = 1} T_{m_i}(xi_i).
+ *
+ * Conventions for every function:
+ *   - Return value: fct_status (FCT_OK == 0).  No function throws or aborts.
+ *     On failure fct_last_error() returns a thread-local message.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device (e.g. a torch tensor's data_ptr).
+ *   - A stream argument is a cudaStream_t passed as void* (NULL = legacy
+ *     default stream).  Device work is asynchronous on that stream unless a
+ *     function says it synchronises.
+ *   - The caller owns every buffer it passes; the library keeps no pointer to
+ *     caller memory after a call returns.  A plan owns its device tables and
+ *     Krylov workspace.  One plan must not run two executes at once.
+ *   - Support order in equals coefficient order out.
+ *   - Layouts: support uint16[N][D]; sizes int32[K][D]; nodes double[K][D];
+ *     samples double[M], grid l's tensor of shape sizes[l] in row-major order
+ *     (last axis fastest), grids concatenated in order, M = sum_l prod_i n_{l,i}.
+ */
+#ifndef FCT_H
+#define FCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FCT_OK = 0,
+  FCT_ERR_INVALID_ARG = 1,  /* malformed sizes, support, options or pointers   */
+  FCT_ERR_RANK = 2,         /* reserved: plan rejected by a rank check          */
+  FCT_ERR_NOCONV = 3,       /* iteration cap reached; best iterate is written   */
+  FCT_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired               */
+  FCT_ERR_OOM = 5,          /* device allocation failed                          */
+  FCT_ERR_NONFINITE = 6,    /* NaN/Inf met in the samples or a reduction         */
+  FCT_ERR_CUDA = 7,         /* any other CUDA runtime error                      */
+  FCT_ERR_NO_DEVICE = 8     /* no usable CUDA device                             */
+} fct_status;
+
+enum { FCT_FP64 = 0, FCT_MIXED = 1 };
+
+/* Function families of fct_sample (synthetic workloads). */
+enum {
+  FCT_FAMILY_POLY = 0,          /* sum_m c_m T_m(x); params = c[N] (support order)        */
+  FCT_FAMILY_GAUSSCOS = 1,      /* exp(-sum a_i x_i^2) cos(sum b_i x_i); params = a[D],b[D] */
+  FCT_FAMILY_RATIONAL = 2,      /* 1/(1 + sum c_i x_i^2); params = c[D]                    */
+  FCT_FAMILY_POLY_GAUSSCOS = 3  /* gausscos + poly; params = a[D], b[D], c[N]              */
+};
+
+typedef struct fct_plan_s* fct_plan;
+
+typedef struct {
+  int precision;      /* FCT_FP64: FP64 CGLS.  FCT_MIXED: FP32 inner CGLS with FP64
+                         residual, FP64 reductions and FP64 refinement sweeps.          */
+  double tol;         /* stop when ||A^T r|| <= tol * ||A^T b|| (FP64 measure)           */
+  int max_iter;       /* cap on CGLS iterations (FP64) / inner iterations per sweep     */
+  double inner_tol;   /* FCT_MIXED: relative tolerance of each inner FP32 solve         */
+  int max_refine;     /* FCT_MIXED: cap on FP64 refinement sweeps                       */
+  int block_threads;  /* 0 = default (256).  Must be 128, 256 or 512 otherwise.         */
+  int max_blocks;     /* 0 = all co-resident blocks; else cap on the solver's grid      */
+  int coef_lanes;     /* 0 = auto; else 1, 2, 4, 8 or 16 threads per coefficient in A^T r */
+  double timeout_s;   /* bound on any device-side wait (default 4 s)                    */
+} fct_options;
+
+typedef struct {
+  int status;                 /* fct_status of this transform                        */
+  int iterations;             /* CGLS iterations (FP64) or inner iterations (mixed)  */
+  int refinements;            /* FP64 refinement sweeps (mixed path)                 */
+  int reserved;
+  double rel_normal_residual; /* ||A^T r|| / ||A^T b|| at exit, FP64                  */
+  double gamma0;              /* ||A^T b||^2                                          */
+} fct_report;
+
+typedef struct {
+  int64_t N;                /* support size (columns)                              */
+  int64_t M;                /* samples over all grids                              */
+  int64_t R;                /* nonempty bins over all grids (rows of A)            */
+  int64_t nnz;              /* K*N                                                 */
+  int32_t D, K;
+  int32_t passes;           /* DCT passes (max active axes over grids)             */
+  int32_t grid_blocks;      /* solver grid size used by fct_execute                */
+  int32_t block_threads;
+  int32_t coef_lanes;
+  int64_t device_bytes;     /* tables + workspace held on the device               */
+} fct_plan_info;
+
+/* Fill *opt with defaults: FP64, tol 1e-13, max_iter 20000, inner_tol 1e-6,
+ * max_refine 6, automatic launch shape, 4 s wait bound. */
+void fct_default_options(fct_options* opt);
+
+/* Thread-local message of the last failing call (never NULL). */
+const char* fct_last_error(void);
+
+/* Human-readable name of a status code. */
+const char* fct_status_string(int status);
+
+/*
+ * Build a plan: the alias tables of every grid (Sec. 3.3, Algorithm 2 without
+ * its condition-number loop; the L-grid is an input), the DCT-I matrices and
+ * the solver workspace, and upload them to the current device.
+ *   D in [1, 255]; N >= 1; support host uint16[N][D] (any multi-indices);
+ *   K >= 1; sizes host int32[K][D], every n >= 1, each grid's point count and
+ *   the total M below 2^31, K*N below 2^31; nodes host double[K][D] in [-1,1]
+ *   (read where n == 1; NULL means xi = 1); opt NULL = defaults.
+ * Synchronous.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_OOM, FCT_ERR_CUDA,
+ * FCT_ERR_NO_DEVICE.  *out is NULL on failure.
+ */
+fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* support,
+                           int K, const int32_t* sizes, const double* nodes,
+                           const fct_options* opt);
+
+/* Plan geometry (host struct). */
+fct_status fct_plan_get_info(fct_plan plan, fct_plan_info* info);
+
+/* offsets host int64[K+1]: start of each grid's samples in the samples array. */
+fct_status fct_grid_offsets(fct_plan plan, int64_t* offsets);
+
+/*
+ * Sample a synthetic function on the plan's L-grid (the "sample f" step of
+ * Algorithm 3).  params host double[nparams] laid out per FCT_FAMILY_*;
+ * samples device double[M].  Asynchronous on stream (params are staged
+ * through plan-owned device memory before returning).
+ */
+fct_status fct_sample(fct_plan plan, int family, const double* params, int64_t nparams,
+                      double* samples, void* stream);
+
+/*
+ * Execute Algorithm 3 on device-resident samples: per-grid DCT-I, bin gather,
+ * CGLS (FP64 or mixed with FP64 refinement), coefficients out.
+ *   samples device double[M] (read only); coeffs device double[N] (written).
+ * One cooperative kernel launch on stream.  If rep != NULL the call waits for
+ * the stream and fills *rep, returning rep->status; otherwise it returns after
+ * the launch (status then only via a later fct_plan_last_report).
+ */
+fct_status fct_execute(fct_plan plan, const double* samples, double* coeffs, void* stream,
+                       fct_report* rep);
+
+/*
+ * fct_execute with HOST buffers: copies samples host double[M] to the device,
+ * executes, copies coeffs back to host double[N], and waits for the stream.
+ * Pinned host memory gives asynchronous copies; pageable memory also works.
+ */
+fct_status fct_execute_host(fct_plan plan, const double* samples_host, double* coeffs_host,
+                            void* stream, fct_report* rep);
+
+/*
+ * Solve B independent transforms in ONE persistent cooperative launch.  Teams
+ * of blocks pull transforms from a device work queue; each transform's result
+ * is bit-identical to its result alone under the same plan.
+ *   plans host fct_plan[B] (distinct plans); samples host array of B device
+ *   pointers; coeffs host array of B device pointers; reps host fct_report[B]
+ *   or NULL (same waiting rule as fct_execute); team_blocks = blocks per team
+ *   (0 = automatic).
+ */
+fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* samples,
+                             double* const* coeffs, int team_blocks, void* stream,
+                             fct_report* reps);
+
+/* Report of the plan's last execute (waits for stream). */
+fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);
+
+/* Release a plan's device memory (synchronises the device first). NULL is OK. */
+fct_status fct_destroy(fct_plan plan);
+
+/*
+ * Host-only alias tables (no device needed), for bit-exact checks:
+ *   bin   host int32[K][N]: row-major bin of column m on grid l (the index of
+ *         its one nonzero within grid l's full DCT output);
+ *   crow  host int32[K][N]: global compressed row of that nonzero, rows
+ *         numbered grid by grid, nonempty bins in ascending bin order;
+ *   weight host double[K][N]: the entry, prod over n_i == 1 of T_{m_i}(xi_i);
+ *   *R_out: number of nonempty rows.  Any output pointer may be NULL.
+ */
+fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,
+                                 const int32_t* sizes, const double* nodes, int32_t* bin,
+                                 int32_t* crow, double* weight, int64_t* R_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCT_H */

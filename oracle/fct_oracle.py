@@ -1,0 +1,401 @@
+"""Plain FP64 CPU oracle for the sparse Fast Chebyshev Transform (Jones et al.,
+"A Sparse Fast Chebyshev Transform for High-Dimensional Approximation").
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import or run this module.
+It shares no code with the CUDA path; the only thing both read is the seeded
+input generator package ``workloads`` (random draws, no arithmetic of the
+method).
+
+What it computes (Algorithm 3, Sec. 3.4): for an L-grid of K tensor grids,
+    b = F f   (per grid, the multi-dimensional DCT-I interpolation coefficients
+               of the samples; Eq. (main_linear_system), rows of empty bins
+               dropped)
+    A         (stacked per-grid alias matrices, Eq. (L-grid_A_mat), entries
+               from the fold relation, the extrema-grid analogue of
+               Lemma (lem:aliasing) / Eq. (aliasing_matrix_nd_diff))
+    c* = argmin_c || b - A c ||_2      (the least-squares problem of Sec. 3.4)
+
+Readings of the paper this oracle follows (each also listed in the design doc):
+  * grid: Chebyshev extrema x_j = cos(pi j / (n-1)), j = 0..n-1, with a DCT-I
+    per axis and an unsigned fold (the paper's first-kind grid / DCT-II form
+    is the ``*_first_kind`` family below);
+  * normalisation: b holds the exact Chebyshev coefficients of the grid
+    interpolant, so A has unit entries times single-point weights;
+  * an axis with one point samples at a given node xi and contributes the
+    weight T_{m_i}(xi) to every entry of that column;
+  * solver: the least-squares minimiser itself (dense Householder QR, normal
+    equations with refinement, or CGLS to a tight tolerance, by size).
+
+Parity pins: every function here is checked by ``tests/test_oracle_pins.py``
+against closed forms, library routines, brute force or invariants.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+import workloads as W
+
+
+# ==========================================================================
+# Sec. 2: Chebyshev polynomials, index sets
+# ==========================================================================
+def chebyshev_T(n, x):
+    """T_n(x) = cos(n arccos x)  (definition, Sec. 2)."""
+    x = np.clip(np.asarray(x, dtype=np.float64), -1.0, 1.0)
+    return np.cos(np.asarray(n, dtype=np.float64) * np.arccos(x))
+
+
+def chebyshev_T_table(nmax: int, x) -> np.ndarray:
+    """[len(x), nmax+1] table of T_0..T_nmax by the three-term recurrence
+    T_{n+1} = 2 x T_n - T_{n-1} (Sec. 2)."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    t = np.empty((x.size, nmax + 1), dtype=np.float64)
+    t[:, 0] = 1.0
+    if nmax >= 1:
+        t[:, 1] = x
+    for n in range(1, nmax):
+        t[:, n + 1] = 2.0 * x * t[:, n] - t[:, n - 1]
+    return t
+
+
+def support_size_total_degree(d: int, D: int) -> int:
+    """|S^1_{d,D}| = C(d + D, d), Eq. (N_1norm)."""
+    return math.comb(d + D, d)
+
+
+def support_total_degree_bruteforce(d: int, D: int) -> np.ndarray:
+    """S^1_{d,D} by filtering the full box {0..d}^D (tiny D only)."""
+    grids = np.meshgrid(*[np.arange(d + 1)] * D, indexing="ij")
+    allm = np.stack([g.reshape(-1) for g in grids], axis=1)
+    return allm[allm.sum(axis=1) <= d]
+
+
+# ==========================================================================
+# Grids and samples
+# ==========================================================================
+def extrema_nodes(n: int, xi: float = 1.0) -> np.ndarray:
+    """Chebyshev extrema x_j = cos(pi j/(n-1)), j = 0..n-1 (reading O-1).
+
+    The angle is reduced exactly: x_{n-1-j} = -x_j is enforced by computing
+    the first half and mirroring, so the endpoints are exactly +-1 and the
+    middle point of an odd grid is exactly 0.  n == 1 is the single node xi.
+    """
+    if n == 1:
+        return np.array([xi], dtype=np.float64)
+    j = np.arange(n)
+    x = np.cos(np.pi * j / (n - 1))
+    half = n // 2
+    x[n - half:] = -x[:half][::-1]
+    if n % 2 == 1:
+        x[half] = 0.0
+    x[0], x[-1] = 1.0, -1.0
+    return x
+
+
+def grid_axes(sizes_l, nodes_l) -> list[np.ndarray]:
+    return [extrema_nodes(int(n), float(xi)) for n, xi in zip(sizes_l, nodes_l)]
+
+
+def _broadcast_axis(v: np.ndarray, i: int, D: int) -> np.ndarray:
+    shape = [1] * D
+    shape[i] = v.size
+    return v.reshape(shape)
+
+
+def sample_grid(family: int, params: np.ndarray, support: np.ndarray, axes) -> np.ndarray:
+    """f on the tensor grid spanned by ``axes`` (row-major tensor)."""
+    D = len(axes)
+    shape = tuple(a.size for a in axes)
+    if family in (W.FAMILY_GAUSSCOS, W.FAMILY_POLY_GAUSSCOS):
+        a, b = params[:D], params[D:2 * D]
+        quad = sum(a[i] * _broadcast_axis(axes[i] ** 2, i, D) for i in range(D))
+        lin = sum(b[i] * _broadcast_axis(axes[i], i, D) for i in range(D))
+        f = np.exp(-quad) * np.cos(lin)
+        if family == W.FAMILY_POLY_GAUSSCOS:
+            f = f + sample_poly_bruteforce(params[2 * D:], support, axes)
+        return np.broadcast_to(f, shape).copy()
+    if family == W.FAMILY_RATIONAL:
+        c = params[:D]
+        quad = sum(c[i] * _broadcast_axis(axes[i] ** 2, i, D) for i in range(D))
+        return np.broadcast_to(1.0 / (1.0 + quad), shape).copy()
+    if family == W.FAMILY_POLY:
+        return sample_poly_bruteforce(params, support, axes)
+    raise ValueError(family)
+
+
+def sample_poly_bruteforce(coeffs: np.ndarray, support: np.ndarray, axes) -> np.ndarray:
+    """p(x) = sum_m c_m prod_i T_{m_i}(x_i) at every grid point, term by term
+    (Eq. (chebyshev_expansion)); T from the recurrence."""
+    D = len(axes)
+    shape = tuple(a.size for a in axes)
+    dmax = int(support.max()) if support.size else 0
+    tabs = [chebyshev_T_table(dmax, ax) for ax in axes]           # [n_i, dmax+1]
+    pts = np.stack(np.meshgrid(*[np.arange(s) for s in shape], indexing="ij"), -1).reshape(-1, D)
+    out = np.zeros(pts.shape[0])
+    sup = support.astype(np.int64)
+    step = max(1, 2_000_000 // max(1, sup.shape[0]))
+    for s0 in range(0, pts.shape[0], step):
+        p = pts[s0:s0 + step]
+        prod = np.ones((p.shape[0], sup.shape[0]))
+        for i in range(D):
+            prod *= tabs[i][p[:, i]][:, sup[:, i]]
+        out[s0:s0 + step] = prod @ coeffs
+    return out.reshape(shape)
+
+
+def sample_lgrid(family, params, support, sizes, nodes) -> np.ndarray:
+    """Concatenated samples of all K grids (row-major per grid)."""
+    return np.concatenate([sample_grid(family, params, support, grid_axes(sizes[l], nodes[l])).ravel()
+                           for l in range(sizes.shape[0])])
+
+
+# ==========================================================================
+# DCT-I (per axis) -- the F^(l) blocks of Eq. (main_linear_system)
+# ==========================================================================
+def dct1_matrix(n: int) -> np.ndarray:
+    """Interpolation DCT-I on n >= 2 extrema points:
+        y_k = (2 e_k/(n-1)) sum_j e_j cos(pi j k/(n-1)) x_j,  e_0 = e_{n-1} = 1/2, else 1,
+    so that samples of sum_k a_k T_k (k < n) map to a.  The cosine argument
+    j k is reduced modulo 2(n-1) in integers first."""
+    j = np.arange(n)
+    jk = np.outer(j, j) % (2 * (n - 1))
+    e = np.ones(n)
+    e[0] = e[-1] = 0.5
+    return (2.0 * e[:, None] / (n - 1)) * e[None, :] * np.cos(np.pi * jk / (n - 1))
+
+
+def dct1_grid(f: np.ndarray) -> np.ndarray:
+    """Apply the DCT-I along every axis with n >= 2 (axes of size 1 are the
+    identity).  Direct O(n^2) per fibre; no fast transform."""
+    y = np.asarray(f, dtype=np.float64)
+    for axis, n in enumerate(y.shape):
+        if n >= 2:
+            y = np.moveaxis(np.tensordot(dct1_matrix(n), y, axes=([1], [axis])), 0, axis)
+    return y
+
+
+# ==========================================================================
+# Aliasing: fold, per-grid alias matrix, stacked system
+# ==========================================================================
+def fold(m, n: int):
+    """Alias of degree m on an n-point extrema grid (n >= 2): T_m and
+    T_fold(m) agree on every node.  r = m mod 2(n-1); fold = r if r <= n-1
+    else 2(n-1) - r."""
+    m = np.asarray(m, dtype=np.int64)
+    period = 2 * (n - 1)
+    r = m % period
+    return np.where(r <= n - 1, r, period - r)
+
+
+def grid_bins(support: np.ndarray, sizes_l) -> np.ndarray:
+    """Row-major linear bin index of every support element on grid l:
+    sum over axes with n_i >= 2 of fold(m_i) * stride_i (Eq.
+    (aliasing_matrix_nd_diff): the column of m has its one nonzero there)."""
+    D = len(sizes_l)
+    strides = np.ones(D, dtype=np.int64)
+    for i in range(D - 2, -1, -1):
+        strides[i] = strides[i + 1] * int(sizes_l[i + 1])
+    sup = support.astype(np.int64)
+    bins = np.zeros(sup.shape[0], dtype=np.int64)
+    for i in range(D):
+        n = int(sizes_l[i])
+        if n >= 2:
+            bins += fold(sup[:, i], n) * strides[i]
+    return bins
+
+
+def grid_weights(support: np.ndarray, sizes_l, nodes_l) -> np.ndarray:
+    """Entry of the column of m: prod over single-point axes of T_{m_i}(xi_i)."""
+    w = np.ones(support.shape[0])
+    for i, n in enumerate(sizes_l):
+        if int(n) == 1:
+            w *= chebyshev_T(support[:, i].astype(np.int64), nodes_l[i])
+    return w
+
+
+def alias_matrix_grid(support, sizes_l, nodes_l) -> sp.csr_matrix:
+    """A^(l) over all T_l bins (T_l x N), one nonzero per column."""
+    T = int(np.prod(np.asarray(sizes_l, dtype=np.int64)))
+    N = support.shape[0]
+    return sp.csr_matrix((grid_weights(support, sizes_l, nodes_l),
+                          (grid_bins(support, sizes_l), np.arange(N))), shape=(T, N))
+
+
+def alias_matrix_grid_bruteforce(support, sizes_l, nodes_l) -> np.ndarray:
+    """A^(l) with no fold formula: column m = DCT-I of T_m sampled on grid l
+    (Eq. (multi_dim_dct) read column by column).  Tiny grids only."""
+    axes = grid_axes(sizes_l, nodes_l)
+    D = len(axes)
+    cols = []
+    for m in support.astype(np.int64):
+        f = np.ones(tuple(a.size for a in axes))
+        for i in range(D):
+            f = f * _broadcast_axis(chebyshev_T(m[i], axes[i]), i, D)
+        cols.append(dct1_grid(f).ravel())
+    return np.stack(cols, axis=1)
+
+
+class AliasSystem:
+    """The stacked least-squares system of Eq. (main_linear_system), rows of
+    empty bins dropped (they do not involve c)."""
+
+    def __init__(self, support, sizes, nodes):
+        self.support = np.asarray(support)
+        self.sizes = np.asarray(sizes)
+        self.nodes = np.asarray(nodes)
+        K = self.sizes.shape[0]
+        self.T = np.prod(self.sizes.astype(np.int64), axis=1)
+        self.offsets = np.concatenate([[0], np.cumsum(self.T)])
+        blocks, self.rows = [], []
+        for l in range(K):
+            Al = alias_matrix_grid(self.support, self.sizes[l], self.nodes[l])
+            nonempty = np.unique(grid_bins(self.support, self.sizes[l]))
+            self.rows.append(nonempty)
+            blocks.append(Al[nonempty])
+        self.A = sp.vstack(blocks).tocsr()
+        self.R = self.A.shape[0]
+
+    def rhs(self, samples: np.ndarray) -> np.ndarray:
+        """b: per grid DCT-I of its samples, restricted to nonempty bins."""
+        out = []
+        for l in range(self.sizes.shape[0]):
+            f = samples[self.offsets[l]:self.offsets[l + 1]].reshape(tuple(int(n) for n in self.sizes[l]))
+            out.append(dct1_grid(f).ravel()[self.rows[l]])
+        return np.concatenate(out)
+
+
+# ==========================================================================
+# Least-squares solvers (Sec. 3.4: "solve ... using CG"; direct forms for pins)
+# ==========================================================================
+class RankDeficient(RuntimeError):
+    pass
+
+
+def householder_lstsq(A: np.ndarray, b: np.ndarray, rank_tol: float = 1e-12) -> np.ndarray:
+    """min ||A c - b|| by Householder QR and back substitution (own code)."""
+    A = np.array(A, dtype=np.float64, copy=True)
+    b = np.array(b, dtype=np.float64, copy=True)
+    m, n = A.shape
+    if m < n:
+        raise RankDeficient("fewer rows than columns")
+    for k in range(n):
+        x = A[k:, k]
+        nx = np.linalg.norm(x)
+        if nx == 0.0:
+            continue
+        alpha = -nx if x[0] >= 0 else nx
+        v = x.copy()
+        v[0] -= alpha
+        nv = np.linalg.norm(v)
+        if nv == 0.0:
+            continue
+        v /= nv
+        A[k:, k:] -= 2.0 * np.outer(v, v @ A[k:, k:])
+        b[k:] -= 2.0 * v * (v @ b[k:])
+    Rm = np.triu(A[:n, :n])
+    diag = np.abs(np.diag(Rm))
+    if diag.min() <= rank_tol * diag.max():
+        raise RankDeficient(f"min |R_kk| / max |R_kk| = {diag.min() / diag.max():.3e}")
+    c = np.zeros(n)
+    for k in range(n - 1, -1, -1):
+        c[k] = (b[k] - Rm[k, k + 1:] @ c[k + 1:]) / Rm[k, k]
+    return c
+
+
+def csne_lstsq(A: sp.spmatrix, b: np.ndarray, refine: int = 4) -> np.ndarray:
+    """Corrected semi-normal equations: Cholesky of A^T A, then corrections
+    c += (A^T A)^{-1} A^T (b - A c).  Medium sizes (N up to ~2e4)."""
+    import scipy.linalg as sla
+    AtA = (A.T @ A).toarray()
+    try:
+        cf = sla.cho_factor(AtA, lower=False, check_finite=False)
+    except np.linalg.LinAlgError as e:
+        raise RankDeficient(str(e))
+    c = sla.cho_solve(cf, A.T @ b, check_finite=False)
+    for _ in range(refine):
+        c = c + sla.cho_solve(cf, A.T @ (b - A @ c), check_finite=False)
+    return c
+
+
+def cgls(A, b: np.ndarray, tol: float = 1e-15, maxit: int = 100000):
+    """Conjugate gradients on the normal equations of min ||A c - b|| (the
+    "CG method" of Sec. 3.4), from c = 0.  Stops when
+    ||A^T r|| <= tol ||A^T b|| or when ||A^T r|| has not improved for 200
+    iterations.  Returns (c, iterations, ||A^T r|| / ||A^T b||)."""
+    x = np.zeros(A.shape[1])
+    r = np.array(b, dtype=np.float64, copy=True)
+    s = A.T @ r
+    p = s.copy()
+    gamma = float(s @ s)
+    gamma0 = gamma
+    if gamma0 == 0.0:
+        return x, 0, 0.0
+    best, best_it, it = math.inf, 0, 0
+    for it in range(1, maxit + 1):
+        q = A @ p
+        delta = float(q @ q)
+        if delta == 0.0:
+            break
+        alpha = gamma / delta
+        x += alpha * p
+        r -= alpha * q
+        s = A.T @ r
+        gnew = float(s @ s)
+        rel = math.sqrt(gnew / gamma0)
+        if rel <= tol:
+            gamma = gnew
+            break
+        if rel < best:
+            best, best_it = rel, it
+        elif it - best_it > 200:
+            gamma = gnew
+            break
+        beta = gnew / gamma
+        p = s + beta * p
+        gamma = gnew
+    return x, it, math.sqrt(gamma / gamma0)
+
+
+def solve(system: AliasSystem, b: np.ndarray, method: str = "auto", tol: float = 1e-15):
+    """The least-squares minimiser c* of Algorithm 3, by the tier that fits."""
+    N = system.A.shape[1]
+    if method == "auto":
+        method = "qr" if N <= 600 else ("csne" if N <= 12000 else "cgls")
+    if method == "qr":
+        return householder_lstsq(system.A.toarray(), b)
+    if method == "lstsq":
+        return np.linalg.lstsq(system.A.toarray(), b, rcond=None)[0]
+    if method == "csne":
+        return csne_lstsq(system.A, b)
+    if method == "cgls":
+        return cgls(system.A, b, tol=tol)[0]
+    raise ValueError(method)
+
+
+def fct(support, sizes, nodes, samples, method: str = "auto", tol: float = 1e-15):
+    """Algorithm 3 end to end on given samples: build A, DCT, solve."""
+    system = AliasSystem(support, sizes, nodes)
+    b = system.rhs(samples)
+    return solve(system, b, method=method, tol=tol)
+
+
+def condition_number(A) -> float:
+    """kappa(A) = sigma_max / sigma_min from the eigenvalues of A^T A (dense;
+    N up to ~1e4).  Returns inf when A^T A is singular to working precision."""
+    AtA = (A.T @ A)
+    AtA = AtA.toarray() if sp.issparse(AtA) else AtA
+    ev = np.linalg.eigvalsh(AtA)
+    if ev[0] <= ev[-1] * 1e-28:
+        return math.inf
+    return math.sqrt(ev[-1] / ev[0])
+
+
+def numerical_rank(A, rtol: float = 1e-10) -> int:
+    AtA = (A.T @ A)
+    AtA = AtA.toarray() if sp.issparse(AtA) else AtA
+    ev = np.linalg.eigvalsh(AtA)
+    return int((ev > ev[-1] * rtol * rtol).sum())

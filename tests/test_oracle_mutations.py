@@ -1,0 +1,107 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that at least
+one pin in test_oracle_pins fails for each.  A pin set that let one of these
+through would not pin the oracle."""
+import numpy as np
+import pytest
+
+from oracle import fct_oracle as O
+from tests import test_oracle_pins as P
+
+
+def _fold_off_by_one(m, n):
+    m = np.asarray(m, dtype=np.int64)
+    period = 2 * (n - 1)
+    r = m % period
+    return np.where(r <= n - 1, r, period - r - 1)
+
+
+def _dct_no_output_weight(n):
+    j = np.arange(n)
+    jk = np.outer(j, j) % (2 * (n - 1))
+    e = np.ones(n)
+    e[0] = e[-1] = 0.5
+    return (2.0 / (n - 1)) * e[None, :] * np.cos(np.pi * jk / (n - 1))
+
+
+_orig_dct = O.dct1_matrix
+_orig_T = O.chebyshev_T
+_orig_nodes = O.extrema_nodes
+_orig_weights = O.grid_weights
+_orig_bins = O.grid_bins
+
+
+def _dct_wrong_period(n):
+    j = np.arange(n)
+    e = np.ones(n)
+    e[0] = e[-1] = 0.5
+    return (2.0 * e[:, None] / (n - 1)) * e[None, :] * np.cos(np.pi * np.outer(j, j) / n)
+
+
+def _weights_dropped(support, sizes_l, nodes_l):
+    return np.ones(support.shape[0])
+
+
+def _bins_colmajor(support, sizes_l):
+    D = len(sizes_l)
+    strides = np.ones(D, dtype=np.int64)
+    for i in range(1, D):
+        strides[i] = strides[i - 1] * int(sizes_l[i - 1])
+    sup = support.astype(np.int64)
+    bins = np.zeros(sup.shape[0], dtype=np.int64)
+    for i in range(D):
+        n = int(sizes_l[i])
+        if n >= 2:
+            bins += O.fold(sup[:, i], n) * strides[i]
+    return bins
+
+
+def _nodes_mirrored(n, xi=1.0):
+    return -_orig_nodes(n, xi)
+
+
+def _T_table_bad(nmax, x):
+    x = np.asarray(x, dtype=np.float64).reshape(-1)
+    t = np.empty((x.size, nmax + 1))
+    t[:, 0] = 1.0
+    if nmax >= 1:
+        t[:, 1] = x
+    for n in range(1, nmax):
+        t[:, n + 1] = x * t[:, n] - t[:, n - 1]
+    return t
+
+
+def _cgls_wrong_sign(A, b, tol=1e-15, maxit=100000):
+    x = np.zeros(A.shape[1]); r = b.copy(); s = A.T @ r; p = s.copy()
+    gamma = float(s @ s); g0 = gamma
+    for it in range(1, 2000):
+        q = A @ p; alpha = gamma / float(q @ q)
+        x += alpha * p; r += alpha * q
+        s = A.T @ r; gn = float(s @ s)
+        if gn <= tol * tol * g0:
+            break
+        p = s + (gn / gamma) * p; gamma = gn
+    return x, it, 0.0
+
+
+MUTATIONS = [
+    ("fold_off_by_one", "fold", _fold_off_by_one, lambda: P.test_fold_identity_exhaustive()),
+    ("fold_off_by_one_recovery", "fold", _fold_off_by_one,
+     lambda: P.test_exact_recovery_of_polynomials_in_support(*P.RECOVERY[1])),
+    ("dct_no_output_weight", "dct1_matrix", _dct_no_output_weight,
+     lambda: [P.test_dct1_closed_forms(*r) for r in P._golden_dct()]),
+    ("dct_wrong_period", "dct1_matrix", _dct_wrong_period, lambda: P.test_dct1_maps_sampled_Tk_to_unit_vector(9)),
+    ("weights_dropped", "grid_weights", _weights_dropped,
+     lambda: P.test_exact_recovery_of_polynomials_in_support(*P.RECOVERY[2])),
+    ("bins_colmajor", "grid_bins", _bins_colmajor, lambda: P.test_alias_matrix_fold_equals_bruteforce(*P.TINY[1])),
+    ("nodes_mirrored", "extrema_nodes", _nodes_mirrored, lambda: P.test_extrema_nodes(5)),
+    ("T_recurrence_bad", "chebyshev_T_table", _T_table_bad,
+     lambda: P.test_chebyshev_definition_recurrence_and_library_agree()),
+    ("cgls_wrong_sign", "cgls", _cgls_wrong_sign, lambda: P.test_solver_tiers_agree_and_are_optimal()),
+]
+
+
+@pytest.mark.parametrize("name,attr,bad,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pins_catch_planted_mistake(name, attr, bad, pin, monkeypatch):
+    monkeypatch.setattr(O, attr, bad)
+    with pytest.raises((AssertionError, O.RankDeficient, np.linalg.LinAlgError, ZeroDivisionError, ValueError)):
+        pin()

@@ -1,0 +1,306 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties an oracle function to something other than itself: a closed
+form derived by hand, a library routine, brute force, an invariant of the
+alias structure, or exact recovery of a polynomial inside the support (the
+consistent system of Eq. (main_linear_system)).  ``test_oracle_mutations.py``
+plants plausible mistakes in the oracle and checks that these pins catch them.
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import numpy.polynomial.chebyshev as npcheb
+import pytest
+import scipy.fft
+
+import workloads as W
+from oracle import fct_oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Sec. 2
+def test_chebyshev_definition_recurrence_and_library_agree():
+    """T_n(x) = cos(n arccos x) and the three-term recurrence (Sec. 2) agree
+    with numpy's Chebyshev series evaluation."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-1, 1, 200), [-1.0, 0.0, 1.0]])
+    tab = O.chebyshev_T_table(40, x)
+    for n in range(41):
+        e = np.zeros(n + 1)
+        e[n] = 1.0
+        ref = npcheb.chebval(x, e)
+        assert np.max(np.abs(tab[:, n] - ref)) < 1e-12
+        assert np.max(np.abs(O.chebyshev_T(n, x) - ref)) < 1e-12
+
+
+def _golden_counts():
+    rows = []
+    with open(os.path.join(GOLDEN, "support_counts.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                D, d, N = (int(v) for v in line.split())
+                rows.append((D, d, N))
+    return rows
+
+
+@pytest.mark.parametrize("D,d,N", _golden_counts())
+def test_support_size_eq_N_1norm(D, d, N):
+    """|S^1_{d,D}| = C(d+D, d) (Eq. (N_1norm)) for the oracle's count and the
+    shared enumerator; brute force over the box where it is small."""
+    assert O.support_size_total_degree(d, D) == N
+    if N <= 50000:
+        sup = W.total_degree_support(D, d)
+        assert sup.shape == (N, D)
+        assert len({tuple(r) for r in sup.tolist()}) == N
+        assert int(sup.astype(np.int64).sum(axis=1).max(initial=0)) <= d
+    if (d + 1) ** D <= 200000:
+        bf = {tuple(r) for r in O.support_total_degree_bruteforce(d, D).tolist()}
+        assert bf == {tuple(r) for r in W.total_degree_support(D, d).tolist()}
+
+
+# ---------------------------------------------------------------- grids
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 8, 9, 33, 64])
+def test_extrema_nodes(n):
+    x = O.extrema_nodes(n)
+    assert x[0] == 1.0 and x[-1] == -1.0
+    assert np.all(np.diff(x) < 0)
+    assert np.array_equal(x, -x[::-1])
+    if n % 2:
+        assert x[n // 2] == 0.0
+    assert np.max(np.abs(x - np.cos(np.pi * np.arange(n) / (n - 1)))) < 1e-15
+
+
+# ---------------------------------------------------------------- DCT-I
+def _golden_dct():
+    rows = []
+    with open(os.path.join(GOLDEN, "dct1_closed_forms.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                n, f, a = line.split("|")
+                rows.append((int(n), [float(v) for v in f.split()], [float(v) for v in a.split()]))
+    return rows
+
+
+@pytest.mark.parametrize("n,f,a", _golden_dct())
+def test_dct1_closed_forms(n, f, a):
+    assert np.allclose(O.dct1_matrix(n) @ np.array(f), np.array(a), atol=1e-15, rtol=0)
+
+
+@pytest.mark.parametrize("n", [2, 3, 5, 9, 17, 33, 100, 446])
+def test_dct1_maps_sampled_Tk_to_unit_vector(n):
+    """DCT-I of T_k sampled on the n extrema is e_k for k < n (interpolation is
+    exact for degree < n)."""
+    x = O.extrema_nodes(n)
+    C = O.dct1_matrix(n)
+    V = np.stack([O.chebyshev_T(k, x) for k in range(n)], axis=1)   # V[j, k] = T_k(x_j)
+    assert np.max(np.abs(C @ V - np.eye(n))) < 1e-12 * max(1, n / 10)
+
+
+@pytest.mark.parametrize("n", [2, 3, 7, 16, 33])
+def test_dct1_matches_scipy_type1(n):
+    """scipy's unnormalised DCT-I y_k = x_0 + (-1)^k x_{n-1} + 2 sum_{j=1}^{n-2}
+    x_j cos(pi j k/(n-1)) relates to ours by a_k = e_k y_k / (n-1)."""
+    rng = np.random.default_rng(n)
+    f = rng.standard_normal(n)
+    y = scipy.fft.dct(f, type=1)
+    e = np.ones(n)
+    e[0] = e[-1] = 0.5
+    assert np.max(np.abs(O.dct1_matrix(n) @ f - e * y / (n - 1))) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(3, 4), (2, 5, 3), (1, 6, 4), (5, 1, 1, 3)])
+def test_dct1_grid_equals_square_vandermonde_solve(shape):
+    """On one tensor grid the multi-dimensional DCT-I is interpolation: it
+    solves V a = f with V[pt, k] = prod_i T_{k_i}(x_{i,pt_i}) over all k in the
+    grid's index box (brute-force linear solve, D <= 4)."""
+    rng = np.random.default_rng(sum(shape))
+    nodes = rng.uniform(-1, 1, len(shape))
+    axes = O.grid_axes(np.array(shape), nodes)
+    f = rng.standard_normal(shape)
+    D = len(shape)
+    idx = list(itertools.product(*[range(s) for s in shape]))
+    V = np.array([[np.prod([O.chebyshev_T(k[i], axes[i][p[i]]) for i in range(D)]) for k in idx] for p in idx])
+    a = np.linalg.solve(V, f.ravel())
+    assert np.max(np.abs(O.dct1_grid(f).ravel() - a)) < 1e-12
+
+
+# ---------------------------------------------------------------- fold
+def test_fold_identity_exhaustive():
+    """T_m(x_j) = T_fold(m)(x_j) on every extrema node (n <= 64, m <= 20 n),
+    in FP64 and in the exact integer form m j = +-fold(m) j (mod 2(n-1))."""
+    for n in range(2, 65):
+        x = O.extrema_nodes(n)
+        m = np.arange(0, 20 * n + 1)
+        fm = O.fold(m, n)
+        assert fm.min() >= 0 and fm.max() <= n - 1
+        assert np.array_equal(fm[:n], np.arange(n))          # no alias below n
+        j = np.arange(n)
+        P = 2 * (n - 1)
+        lhs = np.outer(m, j) % P
+        rhs = np.outer(fm, j) % P
+        assert np.all((lhs == rhs) | (lhs == (P - rhs) % P))
+        err = np.abs(O.chebyshev_T(m[:, None], x[None, :]) - O.chebyshev_T(fm[:, None], x[None, :]))
+        assert err.max() < 1e-9    # cos(n arccos x) at large n loses ~n*eps
+
+
+# ---------------------------------------------------------------- alias matrix
+TINY = [
+    # (D, d, sizes, nodes)
+    (1, 9, [[4]], [[1.0]]),
+    (2, 6, [[3, 4], [5, 1], [1, 2]], [[0.3, 0.1], [0.2, -0.7], [0.45, 0.9]]),
+    (3, 4, [[2, 3, 1], [1, 1, 4], [3, 2, 2]], [[0.1, 0.2, 0.6], [-0.3, 0.8, 0.0], [0.5, 0.5, 0.5]]),
+]
+
+
+@pytest.mark.parametrize("D,d,sizes,nodes", TINY)
+def test_alias_matrix_fold_equals_bruteforce(D, d, sizes, nodes):
+    """A^(l) from the fold formula equals, column by column, the DCT-I of T_m
+    sampled on the grid (no fold formula involved)."""
+    sup = W.total_degree_support(D, d)
+    for sz, nd in zip(np.array(sizes), np.array(nodes)):
+        Af = O.alias_matrix_grid(sup, sz, nd).toarray()
+        Ab = O.alias_matrix_grid_bruteforce(sup, sz, nd)
+        assert np.array_equal(Af != 0, np.abs(Ab) > 1e-12)
+        assert np.max(np.abs(Af - Ab)) < 1e-12
+
+
+def test_alias_invariants():
+    """One nonzero per column per grid (Sec. 3.5); with xi = 1 every entry is 1,
+    so ||A||_F^2 = K N and each grid's rows sum to N."""
+    w = W.config_small_poly()
+    ones = np.ones_like(w.nodes)
+    s = O.AliasSystem(w.support, w.sizes, ones)
+    assert s.A.nnz == w.K * w.N
+    assert np.allclose(s.A.data, 1.0)
+    assert abs(s.A.multiply(s.A).sum() - w.K * w.N) < 1e-9
+    start = 0
+    for l in range(w.K):
+        Rl = len(s.rows[l])
+        blk = s.A[start:start + Rl]
+        assert np.all(np.diff(blk.tocsc().indptr) == 1)
+        assert abs(blk.sum() - w.N) < 1e-9
+        start += Rl
+    # with generic nodes the entry magnitudes are |prod T(xi)| <= 1
+    s2 = O.AliasSystem(w.support, w.sizes, w.nodes)
+    assert np.all(np.abs(s2.A.data) <= 1.0 + 1e-15)
+
+
+def test_adjoint_identity():
+    rng = np.random.default_rng(5)
+    w = W.make_workload("t", 11, 3, 6, 6, 1, 7, W.FAMILY_GAUSSCOS)
+    s = O.AliasSystem(w.support, w.sizes, w.nodes)
+    p = rng.standard_normal(s.A.shape[1])
+    r = rng.standard_normal(s.A.shape[0])
+    lhs, rhs = (s.A @ p) @ r, p @ (s.A.T @ r)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs) + 1e-13
+
+
+# ---------------------------------------------------------------- recovery
+RECOVERY = [
+    ("D1", 21, 1, 12, 5, 2, 9),
+    ("D2", 22, 2, 8, 4, 3, 9),
+    ("D3", 23, 3, 5, 9, 1, 6),
+    ("D4", 24, 4, 4, 12, 1, 5),
+]
+
+
+@pytest.mark.parametrize("name,seed,D,d,K,lo,hi", RECOVERY)
+def test_exact_recovery_of_polynomials_in_support(name, seed, D, d, K, lo, hi):
+    """A polynomial whose coefficients live on the support makes the system
+    consistent (Eq. (main_linear_system)); the least-squares solution is the
+    true coefficient vector.  Samples by brute-force evaluation."""
+    w = W.make_workload(name, seed, D, d, K, lo, hi, W.FAMILY_POLY)
+    s = O.AliasSystem(w.support, w.sizes, w.nodes)
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    b = s.rhs(f)
+    for method in ("qr", "lstsq", "csne"):
+        c = O.solve(s, b, method)
+        assert np.linalg.norm(c - w.coeffs_true) <= 1e-11 * np.linalg.norm(w.coeffs_true), method
+    c, it, rel = O.cgls(s.A, b, tol=1e-15)
+    assert np.linalg.norm(c - w.coeffs_true) <= 1e-11 * np.linalg.norm(w.coeffs_true)
+
+
+def test_config_small_recovers_exactly():
+    w = W.config_small_poly()
+    c = O.fct(w.support, w.sizes, w.nodes, O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes), "qr")
+    assert np.linalg.norm(c - w.coeffs_true) <= 1e-13 * np.linalg.norm(w.coeffs_true)
+
+
+def test_full_grid_is_selection_and_returns_dct_output():
+    """One grid resolving every degree of the support (n_i >= d+1) has no
+    collision: A selects rows, and c* is the DCT output at the support's bins
+    (the classical tensor DCT approach of Sec. 4.2)."""
+    D, d = 3, 4
+    sup = W.total_degree_support(D, d)
+    sizes = np.array([[d + 1, d + 2, d + 1]], dtype=np.int32)
+    nodes = np.ones((1, D))
+    s = O.AliasSystem(sup, sizes, nodes)
+    assert s.R == sup.shape[0]
+    f = O.sample_lgrid(W.FAMILY_RATIONAL, W.rational_params(3, D), sup, sizes, nodes)
+    y = O.dct1_grid(f.reshape(tuple(sizes[0])))
+    c = O.solve(s, s.rhs(f), "qr")
+    assert np.max(np.abs(c - y[tuple(sup.T.astype(np.int64))])) < 1e-14
+
+
+# ---------------------------------------------------------------- solvers
+def test_solver_tiers_agree_and_are_optimal():
+    """Householder QR, LAPACK lstsq, corrected semi-normal equations and CGLS
+    agree on a non-polynomial target, and the answer satisfies the normal
+    equations A^T (b - A c) = 0."""
+    w = W.make_workload("tiers", 31, 4, 5, 12, 1, 6, W.FAMILY_GAUSSCOS)
+    s = O.AliasSystem(w.support, w.sizes, w.nodes)
+    b = s.rhs(O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes))
+    cq = O.solve(s, b, "qr")
+    cl = O.solve(s, b, "lstsq")
+    cn = O.solve(s, b, "csne")
+    cg, it, rel = O.cgls(s.A, b, tol=1e-15)
+    nq = np.linalg.norm(cq)
+    for c in (cl, cn, cg):
+        assert np.linalg.norm(c - cq) <= 1e-12 * nq
+    g = s.A.T @ (b - s.A @ cq)
+    assert np.linalg.norm(g) <= 1e-13 * np.linalg.norm(s.A.T @ b)
+
+
+def test_rank_deficient_plan_is_detected():
+    """All grids sharing one single-point node at x = 1 on the same axis: the
+    polynomial T_1(x_0) - 1 vanishes on every grid, so A loses rank and the
+    QR tier refuses."""
+    D, d = 2, 3
+    sup = W.total_degree_support(D, d)
+    sizes = np.array([[1, 5], [1, 4], [1, 6]], dtype=np.int32)
+    s = O.AliasSystem(sup, sizes, np.ones((3, D)))
+    with pytest.raises(O.RankDeficient):
+        O.householder_lstsq(s.A.toarray(), np.ones(s.R))
+    assert O.numerical_rank(s.A) < sup.shape[0]
+
+
+# ---------------------------------------------------------------- workloads
+def test_alg1_postconditions():
+    """Algorithm 1: sizes in {lo..hi} on drawn axes, 1 elsewhere; the running
+    product first exceeds N at the last drawn axis (or never)."""
+    g = W.stream(7, "sizes")
+    for _ in range(500):
+        D = int(g.integers(1, 12))
+        N = int(g.integers(1, 10000))
+        sizes = W.alg1_sampling_rates(g, N, D, 2, 9)
+        assert sizes.min() >= 1 and sizes.max() <= 9
+        prod = int(np.prod(sizes.astype(np.int64)))
+        drawn = sizes[sizes > 1]
+        # at most one draw past N: dropping the smallest drawn factor leaves <= N
+        assert prod <= N or prod // int(drawn.min()) <= N * 9
+        if prod <= N:
+            assert drawn.size == D       # never crossed: every axis was drawn
+
+
+def test_workload_shapes():
+    w = W.config_small_poly()
+    assert (w.N, w.D, w.K) == (153, 2, 4)
+    assert w.sizes.min() >= 9 and w.sizes.max() <= 33
+    assert w.M == int(np.prod(w.sizes, axis=1).sum())
+    w2 = W.config_d6_gausscos()
+    assert (w2.N, w2.K) == (8008, 18)
