@@ -1,0 +1,10 @@
+"""GB300-native sparse Fast Chebyshev Transform (hot path behind a C ABI).
+
+The transform runs in libfct_gb300.so (hand-written CUDA for sm_103a); the
+modules here only build that library and marshal arguments to it.
+"""
+from .fct import (FCT_FAMILY_GAUSSCOS, FCT_FAMILY_POLY, FCT_FAMILY_POLY_GAUSSCOS,  # noqa: F401
+                  FCT_FAMILY_RATIONAL, FCT_FP64, FCT_MIXED, FctError, Plan, fct_alias_tables_host,
+                  fct_default_options, fct_destroy, fct_execute, fct_execute_batch, fct_execute_host,
+                  fct_grid_offsets, fct_plan_create, fct_plan_get_info, fct_plan_last_report, fct_sample,
+                  lib, library_path)

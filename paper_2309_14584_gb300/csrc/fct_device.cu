@@ -1,0 +1,1509 @@
+// GB300 (sm_103a) device path of the sparse Fast Chebyshev Transform.
+//
+// One cooperative, persistent kernel runs the whole of Algorithm 3 for one or
+// many transforms: the per-grid DCT-I axis passes, the gather of nonempty
+// bins into b, and the least-squares solve (CGLS, the "CG method" of Sec. 3.4)
+// whose every iteration is one alias gather A p (bin-major, over the
+// bin-sorted CSR) and one alias adjoint A^T r (coefficient-major over the
+// per-grid row tables), as in the cost model of Sec. 3.5.
+//
+// Blocks are grouped in teams; a team solves one transform at a time, taken
+// from a work queue, and synchronises through a bounded software barrier in
+// global memory (every wait has a time limit and reports FCT_ERR_TIMEOUT).
+// A CGLS iteration needs two team barriers: the vectors p_new = s + beta p
+// and r_new = r - alpha q are formed on the fly inside the gathers from the
+// previous buffers (double-buffered), so no barrier is spent on the
+// elementwise updates.  All reductions are two-stage with a fixed order
+// (per-chunk block sums, then one sum over chunk partials), so a transform's
+// result does not depend on the team size or on the rest of the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fct_internal.h"
+
+using namespace fct;
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *reinterpret_cast<const volatile int*>(p);
+}
+
+// Loads of data written earlier in the same launch by other blocks bypass L1.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+template <typename T>
+__device__ __forceinline__ void stcg(T* p, T v) {
+  __stcg(p, v);
+}
+
+struct Team {
+  int G;            // blocks in the team
+  int rank;         // this block's rank in the team
+  unsigned int epoch;  // barriers passed so far by this block (same in every block)
+  TeamBarrier* bar;
+  int* err;
+  unsigned long long timeout_ns;
+};
+
+// Team-wide barrier: arrive with a release increment of the team's monotonic
+// counter, wait (bounded) until it reaches G x barrier number.  Returns false
+// when the launch is being abandoned (a wait expired here or elsewhere).
+__device__ bool team_sync(Team& tm) {
+  __shared__ int s_ok;
+  __syncthreads();
+  tm.epoch += 1;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (tm.G > 1) {
+      const unsigned int target = tm.epoch * static_cast<unsigned int>(tm.G);
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&tm.bar->count) : "memory");
+      if (ld_acquire_u32(&tm.bar->count) < target) {
+        const unsigned long long t0 = globaltimer_ns();
+        while (ld_acquire_u32(&tm.bar->count) < target) {
+          if (ld_volatile_i32(tm.err) != 0) {
+            ok = 0;
+            break;
+          }
+          if (globaltimer_ns() - t0 > tm.timeout_ns) {
+            atomicCAS(tm.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
+            ok = 0;
+            break;
+          }
+        }
+      }
+    } else {
+      __threadfence();
+      if (ld_volatile_i32(tm.err) != 0) ok = 0;
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  __syncthreads();
+  return ok;
+}
+
+// Called once by every block of a team when it leaves the launch: the last
+// one out resets the team's counter for the next launch.
+__device__ void team_exit(const Team& tm) {
+  __syncthreads();
+  if (threadIdx.x == 0 && tm.G > 1) {
+    __threadfence();
+    const unsigned int n = atomicAdd(&tm.bar->exits, 1u);
+    if (n == static_cast<unsigned int>(tm.G - 1)) {
+      atomicExch(&tm.bar->count, 0u);
+      atomicExch(&tm.bar->exits, 0u);
+    }
+  }
+}
+
+// Deterministic block sum; the result is valid in thread 0.
+template <int BT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < BT / 32; ++w) r += red[w];
+  }
+  __syncthreads();
+  return r;
+}
+
+// Warp 0: sum of n chunk partials in a fixed order (same value in every
+// block), left in red[BT/32].
+template <int BT>
+__device__ __forceinline__ void warp0_team_sum(const double* part, int n, double* red) {
+  double v = 0.0;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
+    double t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v += t[j];  // lane order: part[lane], part[lane+32], ...
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (threadIdx.x == 0) red[BT / 32] = v;
+}
+
+// All threads: team sum of n partials (used outside the overlapped phases).
+template <int BT>
+__device__ double team_sum(const double* part, int n, double* red) {
+  if (threadIdx.x < 32) warp0_team_sum<BT>(part, n, red);
+  __syncthreads();
+  const double r = red[BT / 32];
+  __syncthreads();
+  return r;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V lane_group_sum(V v, int L) {
+  for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-block shared-memory copy of the block's static share of the index
+// tables.  Every team barrier ends with a gpu-scope acquire, which drops the
+// L1 contents, so table reads from global memory would cost an L2 round trip
+// at every step of the row -> entry -> column chain; staged in shared memory
+// they cost one shared load.  Units beyond the capacity read global memory
+// (same arithmetic, same order, same result).
+//   A units (rows): header {r0, r1, lanes, jbase, pool offset}; pool holds
+//   rowptr[r0..r1] - jbase, then col[jbase .. rowptr[r1]).
+//   B units (coefficients): pool holds crow[l][m0 + i] as [K][coefs_per_chunk].
+// ---------------------------------------------------------------------------
+struct BlockTabs {
+  const int* hdrA;      // [nA][5]
+  const int* hdrB;      // [nB]
+  const int* pool;
+  int cachedA, cachedB;
+  const double* mats;   // DCT matrices (shared copy or global)
+};
+
+template <int BT>
+__device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char* dsm, int smem_bytes, BlockTabs* T) {
+  const int nru = P.n_row_units, ncc = P.n_coef_chunks;
+  const int nA = nru > tm.rank ? (nru - tm.rank + tm.G - 1) / tm.G : 0;
+  const int nB = ncc > tm.rank ? (ncc - tm.rank + tm.G - 1) / tm.G : 0;
+  int off = 0;
+  const double* mats = P.dct_mats;
+  if (P.mats_smem > 0 && static_cast<int>(P.mats_smem * sizeof(double)) <= smem_bytes) {
+    double* m = reinterpret_cast<double*>(dsm);
+    for (int i = threadIdx.x; i < P.mats_smem; i += BT) m[i] = __ldg(P.dct_mats + i);
+    mats = m;
+    off = P.mats_smem * static_cast<int>(sizeof(double));
+  }
+  int* hdrA = reinterpret_cast<int*>(dsm + off);
+  int* hdrB = hdrA + 5 * nA;
+  int* pool = hdrB + nB;
+  const int cap = (smem_bytes - off) / 4 - 5 * nA - nB;  // ints left for the pool
+  int used = 0, cachedA = 0, cachedB = 0;
+  if (cap > 0) {
+    for (int k = 0; k < nA; ++k) {
+      const int u = tm.rank + k * tm.G;
+      const int r0 = __ldg(P.ru_first + u), r1 = __ldg(P.ru_first + u + 1);
+      const int jbase = __ldg(P.rowptr + r0), jend = __ldg(P.rowptr + r1);
+      const int need = (r1 - r0 + 1) + (jend - jbase);
+      if (used + need > cap) break;
+      int* rp = pool + used;
+      for (int i = threadIdx.x; i <= r1 - r0; i += BT) rp[i] = __ldg(P.rowptr + r0 + i) - jbase;
+      int* cl = rp + (r1 - r0 + 1);
+      for (int i = threadIdx.x; i < jend - jbase; i += BT) cl[i] = __ldg(P.col + jbase + i);
+      if (threadIdx.x == 0) {
+        int* h = hdrA + 5 * k;
+        h[0] = r0;
+        h[1] = r1;
+        h[2] = __ldg(P.ru_lanes + u);
+        h[3] = jbase;
+        h[4] = used;
+      }
+      used += need;
+      cachedA = k + 1;
+    }
+    const int cpc = P.coefs_per_chunk;
+    const int64_t N = P.N;
+    for (int k = 0; k < nB; ++k) {
+      const int c = tm.rank + k * tm.G;
+      const int need = P.K * cpc;
+      if (used + need > cap) break;
+      int* cr = pool + used;
+      const int m0 = c * cpc;
+      for (int i = threadIdx.x; i < need; i += BT) {
+        const int l = i / cpc, mm = m0 + i % cpc;
+        cr[i] = mm < P.N ? __ldg(P.crow + l * N + mm) : 0;
+      }
+      if (threadIdx.x == 0) hdrB[k] = used;
+      used += need;
+      cachedB = k + 1;
+    }
+  }
+  __syncthreads();
+  T->hdrA = hdrA;
+  T->hdrB = hdrB;
+  T->pool = pool;
+  T->cachedA = cachedA;
+  T->cachedB = cachedB;
+  T->mats = mats;
+}
+
+// ---------------------------------------------------------------------------
+// DCT-I: full axis pass over one work unit (all BT threads)
+// ---------------------------------------------------------------------------
+template <int BT>
+__device__ void dct_unit(const DevPlan& P, const double* mats, const double* __restrict__ samples, const DctChunk& c) {
+  double* out = (c.out_sel == 1 ? P.y0 : P.y1) + c.base;
+  const double* C = mats + c.mat;
+  const int n = c.n, st = c.stride;
+  const double* in = (c.in_sel == 0 ? samples : (c.in_sel == 1 ? P.y0 : P.y1)) + c.base;
+  const bool ro = c.in_sel == 0;
+  for (int e = c.start + threadIdx.x; e < c.start + c.count; e += BT) {
+    const int k = (e / st) % n;
+    const int base = e - k * st;
+    const double* Ck = C + k * n;
+    double acc = 0.0;
+    if (ro) {
+      for (int j = 0; j < n; ++j) acc = fma(Ck[j], __ldg(in + base + j * st), acc);
+    } else {
+      for (int j = 0; j < n; ++j) acc = fma(Ck[j], ldcg(in + base + j * st), acc);
+    }
+    stcg(out + e, acc);
+  }
+}
+
+// Last pass at a nonempty bin: b[row] = sum_j C[k][j] in[rowbase + j*stride].
+__device__ __forceinline__ double dct_final_row(const DevPlan& P, const double* mats, const double* __restrict__ samples,
+                                                int row) {
+  const GridFinal g = P.gfinal[__ldg(P.rowgrid + row)];
+  const int k = __ldg(P.rowk + row);
+  const int base = __ldg(P.rowbase + row);
+  const double* Ck = mats + g.mat + k * g.n;
+  double acc = 0.0;
+  if (g.in_sel == 0) {
+    for (int j = 0; j < g.n; ++j) acc = fma(Ck[j], __ldg(samples + base + j * g.stride), acc);
+  } else {
+    const double* in = g.in_sel == 1 ? P.y0 : P.y1;
+    for (int j = 0; j < g.n; ++j) acc = fma(Ck[j], ldcg(in + base + j * g.stride), acc);
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Gather units (worker threads = threads 32..BT-1; warp 0 reduces meanwhile)
+//   row unit u: rows ru_first[u] .. ru_first[u+1]-1, ru_lanes[u] lanes per row
+//   coef unit c: coefficients c*coefs_per_chunk ..., coef_lanes lanes each
+// ---------------------------------------------------------------------------
+// Row unit geometry: from the block's shared copy (k < cachedA) or global.
+struct RowUnit {
+  int r0, r1, lc, jbase;
+  const int* rp;   // shared rowptr - jbase (nullptr: global)
+  const int* cl;   // shared col (relative to jbase)
+};
+
+__device__ __forceinline__ RowUnit row_unit_geom(const DevPlan& P, const BlockTabs& T, int u, int k) {
+  RowUnit g;
+  if (k < T.cachedA) {
+    const int* h = T.hdrA + 5 * k;
+    g.r0 = h[0];
+    g.r1 = h[1];
+    g.lc = h[2];
+    g.jbase = h[3];
+    g.rp = T.pool + h[4];
+    g.cl = g.rp + (g.r1 - g.r0 + 1);
+  } else {
+    g.r0 = __ldg(P.ru_first + u);
+    g.r1 = __ldg(P.ru_first + u + 1);
+    g.lc = __ldg(P.ru_lanes + u);
+    g.jbase = 0;
+    g.rp = nullptr;
+    g.cl = nullptr;
+  }
+  return g;
+}
+
+// Row gather: for each value functor, sum over the row's entries of
+// w_j * val(col_j).  Entries are staged four per lane at a time.
+template <typename V, typename WT, int NV, typename Val1, typename Val2>
+__device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
+                                            int k, int wk, int* row_out, bool* lead, Val1 val1, Val2 val2, V* out1,
+                                            V* out2) {
+  const RowUnit g = row_unit_geom(P, T, u, k);
+  const int row = g.r0 + wk / g.lc;
+  const int lane = wk & (g.lc - 1);
+  V a1 = V(0), a2 = V(0);
+  if (row < g.r1) {
+    int ja, jb;
+    if (g.rp) {
+      ja = g.rp[row - g.r0];
+      jb = g.rp[row - g.r0 + 1];
+    } else {
+      ja = __ldg(P.rowptr + row);
+      jb = __ldg(P.rowptr + row + 1);
+    }
+    for (int j0 = ja + lane; j0 < jb; j0 += 4 * g.lc) {
+      int c[4];
+      WT wv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = j0 + i * g.lc;
+        c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
+        wv[i] = j < jb ? __ldg(w + g.jbase + j) : WT(0);
+      }
+      V v1[4], v2[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v1[i] = c[i] >= 0 ? val1(c[i]) : V(0);
+        if (NV > 1) v2[i] = c[i] >= 0 ? val2(c[i]) : V(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c[i] >= 0) {
+          a1 = fma(static_cast<V>(wv[i]), v1[i], a1);
+          if (NV > 1) a2 = fma(static_cast<V>(wv[i]), v2[i], a2);
+        }
+    }
+  }
+  *out1 = lane_group_sum(a1, g.lc);
+  if (NV > 1) *out2 = lane_group_sum(a2, g.lc);
+  *row_out = row;
+  *lead = (row < g.r1) && lane == 0;
+}
+
+template <typename V, typename WT, typename Val>
+__device__ __forceinline__ V row_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u, int k,
+                                        int wk, int* row_out, bool* lead, Val val) {
+  V a, b;
+  row_gather_n<V, WT, 1>(P, T, w, u, k, wk, row_out, lead, val, val, &a, &b);
+  return a;
+}
+
+// Phase-A gather of the interleaved {s, p}: as = sum w s[col], ap = sum w p[col]
+// (ap skipped on the first iteration, when p is not defined yet).
+template <typename V, typename V2, typename WT>
+__device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
+                                             int k, int wk, int* row_out, bool* lead, const V2* sp, bool first, V* as,
+                                             V* ap) {
+  const RowUnit g = row_unit_geom(P, T, u, k);
+  const int row = g.r0 + wk / g.lc;
+  const int lane = wk & (g.lc - 1);
+  V a1 = V(0), a2 = V(0);
+  if (row < g.r1) {
+    int ja, jb;
+    if (g.rp) {
+      ja = g.rp[row - g.r0];
+      jb = g.rp[row - g.r0 + 1];
+    } else {
+      ja = __ldg(P.rowptr + row);
+      jb = __ldg(P.rowptr + row + 1);
+    }
+    for (int j0 = ja + lane; j0 < jb; j0 += 4 * g.lc) {
+      int c[4];
+      WT wv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = j0 + i * g.lc;
+        c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
+        wv[i] = j < jb ? __ldg(w + g.jbase + j) : WT(0);
+      }
+      V2 v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (c[i] >= 0) v[i] = ldcg(sp + c[i]);
+        else { v[i].x = V(0); v[i].y = V(0); }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c[i] >= 0) {
+          a1 = fma(static_cast<V>(wv[i]), v[i].x, a1);
+          if (!first) a2 = fma(static_cast<V>(wv[i]), v[i].y, a2);
+        }
+    }
+  }
+  *as = lane_group_sum(a1, g.lc);
+  *ap = lane_group_sum(a2, g.lc);
+  *row_out = row;
+  *lead = (row < g.r1) && lane == 0;
+}
+
+// Coefficient gather: acc = sum over grids l (this lane's share, l = lane,
+// lane + L, ...) of w[l][m] * val(crow[l][m]); up to 8 entries per lane are
+// staged together.
+template <typename V, typename WT, typename Val>
+__device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int c, int k,
+                                         int wk, int* m_out, bool* lead, Val val) {
+  const int L = P.coef_lanes;
+  const int cpc = P.coefs_per_chunk;
+  const int mi = wk / L;
+  const int m = c * cpc + mi;
+  const int lane = wk & (L - 1);
+  const int* cr = k < T.cachedB ? T.pool + T.hdrB[k] : nullptr;
+  V acc = V(0);
+  if (m < P.N) {
+    const int64_t N = P.N;
+    for (int lb = lane; lb < P.K; lb += 8 * L) {
+      int idx[8];
+      WT wv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int l = lb + i * L;
+        idx[i] = l < P.K ? (cr ? cr[l * cpc + mi] : __ldg(P.crow + l * N + m)) : -1;
+        wv[i] = l < P.K ? __ldg(w + l * N + m) : WT(0);
+      }
+      V v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = idx[i] >= 0 ? val(idx[i]) : V(0);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (idx[i] >= 0) acc = fma(static_cast<V>(wv[i]), v[i], acc);
+    }
+  }
+  acc = lane_group_sum(acc, L);
+  *m_out = m;
+  *lead = (m < P.N) && lane == 0;
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Conjugate gradients on the normal equations A^T A x = A^T b, i.e. the CG
+// method applied to the least-squares problem of Sec. 3.4 (CGLS in its
+// normal-residual form), from x = 0 with s = A^T b, p = s:
+//   q = A p;  alpha = |s|^2/|q|^2;  x += alpha p;  s -= alpha A^T q;
+//   beta = |s|^2_new / |s|^2;  p = s + beta p.
+// One team barrier per matrix product:
+//   phase A: q = A s + beta A p from one 16-byte gather of {s, p} per entry,
+//            while warp 0 reduces |s|^2 of the previous phase B;
+//   phase B: t = A^T q while warp 0 reduces |q|^2; the coefficient owner
+//            then writes {s - alpha t, s + beta p} and x + alpha p in place.
+// Workers stream through the block's units without block-wide syncs; each
+// unit's |q|^2 or |s|^2 partial is the fixed-order sum of its warps' sums,
+// so partials (and the result) do not depend on the team size.
+// V2 = {s, p} vector type (double2 / float2), XT = type of x.  Reductions are
+// FP64.  On entry sp[m].x = right-hand side, x = 0, gamma0 = |s|^2.  Stops
+// when sqrt(gamma/gamma0) <= tol, after max_iter (FCT_ERR_NOCONV) or, if
+// stall > 0, when gamma has not decreased for `stall` iterations.
+// ---------------------------------------------------------------------------
+constexpr int kUnitGroup = 16;  // units per flush of the per-warp partials
+
+template <typename V> struct Vec2;
+template <> struct Vec2<double> { using T = double2; };
+template <> struct Vec2<float> { using T = float2; };
+
+template <int BT, typename V, typename WT, typename XT>
+__device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const WT* wcsr, const WT* wcm,
+                          typename Vec2<V>::T* sp, V* q, XT* x, double gamma0, double tol, int max_iter, int stall,
+                          int* iters_out, double* gamma_out, int* status_out, double* red) {
+  using V2 = typename Vec2<V>::T;
+  constexpr int NW = BT / 32 - 1;  // worker warps
+  __shared__ double wpart[kUnitGroup][NW];
+  *status_out = FCT_OK;
+  *iters_out = 0;
+  *gamma_out = gamma0;
+  if (!(gamma0 > 0.0)) {
+    if (!isfinite(gamma0)) *status_out = FCT_ERR_NONFINITE;
+    return true;
+  }
+  const int nru = P.n_row_units, ncc = P.n_coef_chunks;
+  const int wk = static_cast<int>(threadIdx.x) - 32;  // worker index; warp 0 has wk < 0
+  const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
+  const int lane32 = threadIdx.x & 31;
+  double gamma = gamma0, best = gamma0;
+  int it = 0, best_it = 0;
+  bool first = true;
+  // per-warp partial of the k-th unit of the current group -> shared
+  auto warp_part = [&](int kk, double v) {
+    v = warp_sum(v);
+    if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
+  };
+  // flush: unit partial = sum of its warps' partials, in warp order
+  auto flush = [&](double* part, int u0, int nk) {
+    __syncthreads();
+    if (threadIdx.x < nk) {
+      double v = 0.0;
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) v += wpart[threadIdx.x][w2];
+      stcg(part + u0 + threadIdx.x * tm.G, v);
+    }
+    __syncthreads();
+  };
+  for (;;) {
+    // ================= phase A: q = A s + beta A p
+    double beta = 0.0;
+    {
+      auto gather_a = [&](int u, int k, V* as, V* ap, int* row, bool* lead) {
+        row_gather_sp<V, V2, WT>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
+      };
+      int u = tm.rank;
+      V as = V(0), ap = V(0);
+      int row = 0;
+      bool lead = false;
+      if (wk >= 0) {
+        if (u < nru) gather_a(u, 0, &as, &ap, &row, &lead);
+      } else if (!first) {
+        warp0_team_sum<BT>(P.part_c, ncc, red);
+      }
+      __syncthreads();
+      bool done = false;
+      if (!first) {
+        const double gnew = red[BT / 32];
+        ++it;
+        if (!isfinite(gnew)) {
+          *status_out = FCT_ERR_NONFINITE;
+          done = true;
+        } else {
+          beta = gnew / gamma;
+          gamma = gnew;
+          if (sqrt(gamma / gamma0) <= tol) {
+            done = true;
+          } else if (it >= max_iter) {
+            *status_out = FCT_ERR_NOCONV;
+            done = true;
+          } else if (stall > 0) {
+            if (gamma < best) {
+              best = gamma;
+              best_it = it;
+            } else if (it - best_it >= stall) {
+              done = true;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      if (done) break;
+      int k = 0, kg = 0, u0 = u;
+      for (; u < nru; u += tm.G, ++k) {
+        if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
+        double part = 0.0;
+        if (wk >= 0 && lead) {
+          const V qv = first ? as : fma(static_cast<V>(beta), ap, as);
+          stcg(q + row, qv);
+          part = static_cast<double>(qv) * static_cast<double>(qv);
+        }
+        warp_part(kg, part);
+        if (++kg == kUnitGroup) {
+          flush(P.part_r, u0, kg);
+          kg = 0;
+          u0 = u + tm.G;
+        }
+      }
+      if (kg > 0) flush(P.part_r, u0, kg);
+      if (!team_sync(tm)) return false;
+    }
+    // ================= phase B: t = A^T q; {s, p} and x updated by the owner
+    {
+      const int L = P.coef_lanes;
+      auto own_load = [&](int c, V2* o, XT* xo) {
+        const int m = c * P.coefs_per_chunk + wk / L;
+        if ((wk & (L - 1)) == 0 && m < P.N) {
+          *o = ldcg(sp + m);
+          *xo = ldcg(x + m);
+        }
+      };
+      int c = tm.rank;
+      V t = V(0);
+      int m = 0;
+      bool lead = false;
+      V2 o{};
+      XT xo = XT(0);
+      if (wk >= 0) {
+        if (c < ncc) {
+          own_load(c, &o, &xo);
+          t = coef_gather<V, WT>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
+        }
+      } else {
+        warp0_team_sum<BT>(P.part_r, nru, red);
+      }
+      __syncthreads();
+      const double delta = red[BT / 32];
+      __syncthreads();
+      if (!isfinite(delta)) {
+        *status_out = FCT_ERR_NONFINITE;
+        break;
+      }
+      if (!(delta > 0.0)) break;  // q = 0: s is already zero to working precision
+      const double alpha = gamma / delta;
+      int k = 0, kg = 0, c0 = c;
+      for (; c < ncc; c += tm.G, ++k) {
+        if (k > 0 && wk >= 0) {
+          own_load(c, &o, &xo);
+          t = coef_gather<V, WT>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
+        }
+        double part = 0.0;
+        if (wk >= 0 && lead) {
+          const V pn = first ? o.x : fma(static_cast<V>(beta), o.y, o.x);
+          const V sn = fma(static_cast<V>(-alpha), t, o.x);
+          V2 nv;
+          nv.x = sn;
+          nv.y = pn;
+          stcg(sp + m, nv);
+          stcg(x + m, static_cast<XT>(fma(static_cast<XT>(alpha), static_cast<XT>(pn), xo)));
+          part = static_cast<double>(sn) * static_cast<double>(sn);
+        }
+        warp_part(kg, part);
+        if (++kg == kUnitGroup) {
+          flush(P.part_c, c0, kg);
+          kg = 0;
+          c0 = c + tm.G;
+        }
+      }
+      if (kg > 0) flush(P.part_c, c0, kg);
+      if (!team_sync(tm)) return false;
+    }
+    first = false;
+  }
+  *iters_out = it;
+  *gamma_out = gamma;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// One transform on the team (Algorithm 3): DCT-I of every grid, b at the
+// nonempty bins, then the FP64 solve, or FP64 normal-residual sweeps around
+// FP32 inner solves (mixed).
+// ---------------------------------------------------------------------------
+template <int BT>
+__device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned char* dsm, int smem_bytes) {
+  const DevPlan& P = *J.plan;
+  BlockTabs T;
+  load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T);
+  const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units;
+  const int wk = static_cast<int>(threadIdx.x) - 32;
+  const int nce = (P.N + BT - 1) / BT;  // elementwise units over coefficients
+  // ---- full DCT-I axis passes
+  for (int pass = 0; pass < P.npass; ++pass) {
+    const int c0 = __ldg(P.pass_chunk_off + pass), c1 = __ldg(P.pass_chunk_off + pass + 1);
+    for (int c = c0 + tm.rank; c < c1; c += tm.G) dct_unit<BT>(P, T.mats, J.samples, P.dct_chunks[c]);
+    if (!team_sync(tm)) return false;
+  }
+  // ---- last pass at the nonempty bins -> b ; x = 0
+  for (int u = tm.rank; u < nre + nce; u += tm.G) {
+    if (u < nre) {
+      const int row = u * BT + threadIdx.x;
+      if (row < P.R) stcg(P.b + row, dct_final_row(P, T.mats, J.samples, row));
+    } else {
+      const int m = (u - nre) * BT + threadIdx.x;
+      if (m < P.N) stcg(J.coeffs + m, 0.0);
+    }
+  }
+  if (!team_sync(tm)) return false;
+  // ---- s = A^T b, gamma0 = |A^T b|^2
+  for (int c = tm.rank, k = 0; c < ncc; c += tm.G, ++k) {
+    int m = 0;
+    bool lead = false;
+    double t = 0.0;
+    if (wk >= 0) t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
+    double part = 0.0;
+    if (lead) {
+      stcg(P.sp + m, make_double2(t, 0.0));
+      part = t * t;
+    }
+    part = block_sum<BT>(part, red);
+    if (threadIdx.x == 0) stcg(P.part_c + c, part);
+  }
+  if (!team_sync(tm)) return false;
+  const double gamma0 = team_sum<BT>(P.part_c, ncc, red);
+
+  int status = FCT_OK, iters = 0, refines = 0;
+  double gfinal = gamma0;
+  if (!isfinite(gamma0)) {
+    status = FCT_ERR_NONFINITE;
+  } else if (J.precision != FCT_MIXED) {
+    if (!cg_normal<BT, double, double, double>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, J.coeffs, gamma0, J.tol,
+                                               J.max_iter, 0, &iters, &gfinal, &status, red))
+      return false;
+  } else if (gamma0 > 0.0) {
+    // Mixed.  g_k = A^T (b - A x_k) in FP64 (g_0 = A^T b); stop when
+    // |g_k| <= tol |A^T b|; else solve A^T A d = g_k / |A^T b| in FP32 and
+    // set x_{k+1} = x_k + |A^T b| d.
+    const double cs = sqrt(gamma0), ci = 1.0 / cs;
+    double* x = J.coeffs;
+    for (int u = tm.rank; u < nce; u += tm.G) {
+      const int m = u * BT + threadIdx.x;
+      if (m < P.N) {
+        stcg(P.sp32 + m, make_float2(static_cast<float>(ldcg(P.sp + m).x * ci), 0.0f));
+        stcg(P.dx32 + m, 0.0f);
+      }
+    }
+    if (!team_sync(tm)) return false;
+    double g64 = gamma0;
+    for (int k = 0;; ++k) {
+      int it_in = 0, st_in = FCT_OK;
+      double g_in = 0.0;
+      ++refines;
+      if (!cg_normal<BT, float, float, float>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32, g64 * ci * ci,
+                                              J.inner_tol, J.max_iter, 64, &it_in, &g_in, &st_in, red))
+        return false;
+      iters += it_in;
+      if (st_in == FCT_ERR_NONFINITE) {
+        status = st_in;
+        break;
+      }
+      // x += |A^T b| d
+      for (int u = tm.rank; u < nce; u += tm.G) {
+        const int m = u * BT + threadIdx.x;
+        if (m < P.N) stcg(x + m, fma(cs, static_cast<double>(ldcg(P.dx32 + m)), ldcg(x + m)));
+      }
+      if (!team_sync(tm)) return false;
+      // r = b - A x  (FP64)
+      for (int u = tm.rank, k = 0; u < nru; u += tm.G, ++k) {
+        if (wk < 0) continue;
+        int row = 0;
+        bool lead = false;
+        const double ax =
+            row_gather<double, double>(P, T, P.wcsr, u, k, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
+        if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
+      }
+      if (!team_sync(tm)) return false;
+      // g = A^T r (FP64); next inner right-hand side s32 = g / |A^T b|, d = 0
+      for (int c = tm.rank, k = 0; c < ncc; c += tm.G, ++k) {
+        int m = 0;
+        bool lead = false;
+        double t = 0.0;
+        if (wk >= 0)
+          t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
+        double part = 0.0;
+        if (lead) {
+          stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));
+          stcg(P.dx32 + m, 0.0f);
+          part = t * t;
+        }
+        part = block_sum<BT>(part, red);
+        if (threadIdx.x == 0) stcg(P.part_c + c, part);
+      }
+      if (!team_sync(tm)) return false;
+      g64 = team_sum<BT>(P.part_c, ncc, red);
+      gfinal = g64;
+      if (!isfinite(g64)) {
+        status = FCT_ERR_NONFINITE;
+        break;
+      }
+      if (!(g64 > 0.0) || sqrt(g64 / gamma0) <= J.tol) break;
+      if (k + 1 >= J.max_refine) {
+        status = FCT_ERR_NOCONV;
+        break;
+      }
+    }
+  }
+  if (tm.rank == 0 && threadIdx.x == 0) {
+    fct_report rep;
+    rep.status = status;
+    rep.iterations = iters;
+    rep.refinements = refines;
+    rep.reserved = 0;
+    rep.rel_normal_residual = gamma0 > 0.0 ? sqrt(gfinal / gamma0) : 0.0;
+    rep.gamma0 = gamma0;
+    *J.report = rep;
+  }
+  return true;
+}
+
+struct SolveArgs {
+  SolveJob single;          // used when jobs == nullptr
+  const SolveJob* jobs;     // device array of njobs jobs, or nullptr
+  int njobs;
+  int team_blocks;
+  LaunchState* ls;
+  unsigned long long timeout_ns;
+  int smem_bytes;           // dynamic shared memory per block
+};
+
+template <int BT>
+__global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs a) {
+  __shared__ double red[BT / 32 + 2];
+  __shared__ int s_job;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  const int team = blockIdx.x / a.team_blocks;
+  Team tm;
+  tm.G = a.team_blocks;
+  tm.rank = blockIdx.x % a.team_blocks;
+  tm.epoch = 0;
+  tm.bar = &a.ls->bars[team];
+  tm.err = &a.ls->err;
+  tm.timeout_ns = a.timeout_ns;
+  if (a.jobs == nullptr) {
+    if (team == 0 && solve_job<BT>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
+    return;
+  }
+  for (;;) {
+    if (tm.rank == 0 && threadIdx.x == 0) a.ls->team_job[team] = static_cast<int>(atomicAdd(&a.ls->queue_head, 1u));
+    if (!team_sync(tm)) return;
+    if (threadIdx.x == 0) s_job = ldcg(&a.ls->team_job[team]);
+    __syncthreads();
+    const int j = s_job;
+    __syncthreads();
+    if (j >= a.njobs) break;
+    if (!solve_job<BT>(a.jobs[j], tm, red, dsm, a.smem_bytes)) return;
+  }
+  team_exit(tm);
+}
+
+// ---------------------------------------------------------------------------
+// Sampler (workload generator, "sample f" of Algorithm 3)
+// ---------------------------------------------------------------------------
+struct SampleArgs {
+  const int32_t* sizes;      // [K*D]
+  const int64_t* offsets;    // [K+1]
+  const int32_t* node_off;   // [K*D]
+  const double* node_pos;
+  const double* ttab;        // [node count][dmax+1] T_k at every node (poly families)
+  const uint16_t* support;   // [N*D]
+  const double* params;
+  double* out;
+  int64_t M;
+  int K, D, N, family, dmax;
+};
+
+__global__ void cheb_table_kernel(const double* node_pos, int nnodes, int dmax, double* ttab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nnodes) return;
+  const double x = node_pos[j];
+  double* t = ttab + static_cast<int64_t>(j) * (dmax + 1);
+  double t0 = 1.0, t1 = x;
+  t[0] = 1.0;
+  if (dmax >= 1) t[1] = x;
+  for (int k = 1; k < dmax; ++k) {
+    const double t2 = 2.0 * x * t1 - t0;
+    t[k + 1] = t2;
+    t0 = t1;
+    t1 = t2;
+  }
+}
+
+__global__ void sample_kernel(const SampleArgs a) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= a.M) return;
+  int l = 0;
+  while (a.offsets[l + 1] <= e) ++l;
+  int64_t rem = e - a.offsets[l];
+  // axis indices, last axis fastest
+  constexpr int kLocalD = 32;
+  int idx[kLocalD];
+  const bool local = a.D <= kLocalD;
+  double q = 0.0, lin = 0.0;
+  const double* pa = a.params;
+  for (int i = a.D - 1; i >= 0; --i) {
+    const int n = a.sizes[l * a.D + i];
+    const int j = static_cast<int>(rem % n);
+    rem /= n;
+    if (local) idx[i] = a.node_off[l * a.D + i] + j;
+    const double x = a.node_pos[a.node_off[l * a.D + i] + j];
+    if (a.family == FCT_FAMILY_GAUSSCOS || a.family == FCT_FAMILY_POLY_GAUSSCOS) {
+      q = fma(pa[i], x * x, q);
+      lin = fma(pa[a.D + i], x, lin);
+    } else if (a.family == FCT_FAMILY_RATIONAL) {
+      q = fma(pa[i], x * x, q);
+    }
+  }
+  double f = 0.0;
+  if (a.family == FCT_FAMILY_GAUSSCOS || a.family == FCT_FAMILY_POLY_GAUSSCOS) f = exp(-q) * cos(lin);
+  if (a.family == FCT_FAMILY_RATIONAL) f = 1.0 / (1.0 + q);
+  if (a.family == FCT_FAMILY_POLY || a.family == FCT_FAMILY_POLY_GAUSSCOS) {
+    const double* c = a.family == FCT_FAMILY_POLY ? pa : pa + 2 * a.D;
+    const int stride = a.dmax + 1;
+    double acc = 0.0;
+    for (int m = 0; m < a.N; ++m) {
+      const uint16_t* mi = a.support + static_cast<int64_t>(m) * a.D;
+      double t = __ldg(c + m);
+      for (int i = 0; i < a.D; ++i) {
+        int node;
+        if (local) {
+          node = idx[i];
+        } else {
+          int64_t r2 = e - a.offsets[l];
+          for (int k = a.D - 1; k > i; --k) r2 /= a.sizes[l * a.D + k];
+          node = a.node_off[l * a.D + i] + static_cast<int>(r2 % a.sizes[l * a.D + i]);
+        }
+        t *= __ldg(a.ttab + static_cast<int64_t>(node) * stride + __ldg(mi + i));
+      }
+      acc += t;
+    }
+    f += acc;
+  }
+  a.out[e] = f;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+struct fct_plan_s {
+  int device = 0;
+  fct_options opt{};
+  HostTables H;
+  int D = 0, K = 0;
+  int64_t N = 0, M = 0, R = 0;
+  int dmax = 0;
+  std::vector<int32_t> sizes;
+  // device memory
+  char* dmem = nullptr;
+  size_t dbytes = 0;
+  DevPlan hp{};
+  DevPlan* dp = nullptr;
+  LaunchState* ls = nullptr;
+  fct_report* drep = nullptr;
+  SolveJob* djobs = nullptr;     // batch job array (grown on demand)
+  int djobs_cap = 0;
+  // sampler
+  int32_t* d_sizes = nullptr;
+  int64_t* d_offsets = nullptr;
+  int32_t* d_node_off = nullptr;
+  double* d_node_pos = nullptr;
+  uint16_t* d_support = nullptr;
+  double* d_ttab = nullptr;
+  double* d_params = nullptr;
+  int64_t params_cap = 0;
+  // host-buffer execute staging
+  double* d_stage_in = nullptr;
+  double* d_stage_out = nullptr;
+  // launch shape
+  int block_threads = 256;
+  int grid_blocks = 0;
+  int max_coresident = 0;
+  int blocks_per_sm = 1;
+  int smem_bytes = 0;          // dynamic shared memory requested per block
+  int smem_cap = 0;            // largest request that keeps blocks_per_sm resident
+  std::vector<int32_t> ru_first, rowptr_h;  // for the shared-memory sizing of other team sizes
+  bool dirty_state = false;
+};
+
+namespace {
+
+fct_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(FCT_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+    return fail(FCT_ERR_NO_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+  return fail(FCT_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FCT_CUDA(call)                                \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <int BT>
+const void* kernel_ptr() {
+  return reinterpret_cast<const void*>(&fct_solve_kernel<BT>);
+}
+
+const void* solve_kernel_for(int bt) {
+  switch (bt) {
+    case 128: return kernel_ptr<128>();
+    case 512: return kernel_ptr<512>();
+    default: return kernel_ptr<256>();
+  }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_t st) {
+  // Reset the per-launch header (queue head, error flag); team barriers are
+  // self-cleaning and re-zeroed only after an abandoned launch.
+  // Single-transform launches need no reset (team counters reset themselves at
+  // exit); batched launches reset the queue head; after an abandoned launch
+  // the whole state is cleared.
+  if (P->dirty_state) {
+    FCT_CUDA(cudaMemsetAsync(args.ls, 0, sizeof(LaunchState), st));
+  } else if (args.jobs != nullptr) {
+    FCT_CUDA(cudaMemsetAsync(args.ls, 0, offsetof(LaunchState, team_job), st));
+  }
+  P->dirty_state = false;
+  void* kargs[] = {const_cast<SolveArgs*>(&args)};
+  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads), dim3(grid), dim3(P->block_threads), kargs,
+                                       static_cast<size_t>(args.smem_bytes), st));
+  return FCT_OK;
+}
+
+// Shared memory (bytes) a block of rank `rank` in a team of G blocks needs to
+// stage its table share (see load_block_tabs).
+size_t block_smem_need(const fct_plan P, int G, int rank) {
+  const DevPlan& hp = P->hp;
+  size_t ints = 0;
+  int nA = 0, nB = 0;
+  for (int u = rank; u < hp.n_row_units; u += G, ++nA) {
+    const int r0 = P->ru_first[u], r1 = P->ru_first[u + 1];
+    ints += (r1 - r0 + 1) + (P->rowptr_h[r1] - P->rowptr_h[r0]);
+  }
+  for (int c = rank; c < hp.n_coef_chunks; c += G, ++nB) ints += static_cast<size_t>(hp.K) * hp.coefs_per_chunk;
+  ints += 5 * nA + nB;
+  return static_cast<size_t>(hp.mats_smem) * sizeof(double) + 4 * ints;
+}
+
+size_t team_smem_need(const fct_plan P, int G) {
+  size_t need = 0;
+  for (int r = 0; r < G; ++r) need = std::max(need, block_smem_need(P, G, r));
+  return need;
+}
+
+fct_status choose_shape(fct_plan P) {
+  int dev = 0;
+  FCT_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  FCT_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (!prop.cooperativeLaunch) return fail(FCT_ERR_CUDA, "device does not support cooperative launch");
+  const void* kfn = solve_kernel_for(P->block_threads);
+  cudaFuncAttributes fa;
+  FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
+  int per_sm = 0;
+  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->block_threads, 0));
+  if (per_sm < 1) return fail(FCT_ERR_CUDA, "solver kernel cannot be resident");
+  // shared memory each block may take without lowering the blocks per SM
+  const int reserve = 1024;  // per-block system reservation
+  int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / per_sm) - reserve - static_cast<int>(fa.sharedSizeBytes);
+  cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
+  cap = std::max(cap, 0) & ~15;
+  FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  P->blocks_per_sm = per_sm;
+  P->smem_cap = cap;
+  P->max_coresident = per_sm * prop.multiProcessorCount;
+  int units = std::max({P->hp.n_row_units, P->hp.n_coef_chunks, P->hp.n_rowel_chunks, 1});
+  for (int p = 0; p < P->H.npass; ++p)
+    units = std::max(units, P->H.pass_chunk_off[p + 1] - P->H.pass_chunk_off[p]);
+  int g = std::min(P->max_coresident, units);
+  if (P->opt.max_blocks > 0) g = std::min(g, P->opt.max_blocks);
+  P->grid_blocks = std::max(g, 1);
+  P->smem_bytes = static_cast<int>(std::min<size_t>(team_smem_need(P, P->grid_blocks), cap) + 15) & ~15;
+  P->smem_bytes = std::min(P->smem_bytes, cap);
+  int chk = 0;
+  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, kfn, P->block_threads, P->smem_bytes));
+  if (chk * prop.multiProcessorCount < P->grid_blocks) return fail(FCT_ERR_CUDA, "solver grid does not fit");
+  return FCT_OK;
+}
+
+SolveJob make_job(fct_plan P, const double* samples, double* coeffs, fct_report* drep) {
+  SolveJob j{};
+  j.plan = P->dp;
+  j.samples = samples;
+  j.coeffs = coeffs;
+  j.report = drep;
+  j.precision = P->opt.precision;
+  j.max_iter = P->opt.max_iter;
+  j.max_refine = P->opt.max_refine;
+  j.tol = P->opt.tol;
+  j.inner_tol = P->opt.inner_tol;
+  return j;
+}
+
+unsigned long long timeout_ns(fct_plan P) {
+  double t = P->opt.timeout_s > 0 ? P->opt.timeout_s : 4.0;
+  return static_cast<unsigned long long>(t * 1e9);
+}
+
+}  // namespace
+
+extern "C" {
+
+fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* support, int K, const int32_t* sizes,
+                           const double* nodes, const fct_options* opt) {
+  if (!out) return fail(FCT_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  fct_options o;
+  fct_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != FCT_FP64 && o.precision != FCT_MIXED) return fail(FCT_ERR_INVALID_ARG, "bad precision");
+  if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_refine < 0 || !(o.inner_tol > 0.0))
+    return fail(FCT_ERR_INVALID_ARG, "bad tolerance or iteration cap");
+  if (o.block_threads == 0) o.block_threads = 256;
+  if (o.block_threads != 128 && o.block_threads != 256 && o.block_threads != 512)
+    return fail(FCT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+  if (o.coef_lanes != 0 && (o.coef_lanes < 1 || o.coef_lanes > 16 || (o.coef_lanes & (o.coef_lanes - 1))))
+    return fail(FCT_ERR_INVALID_ARG, "coef_lanes must be 0 or a power of two <= 16");
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev < 1) return fail(FCT_ERR_NO_DEVICE, "no CUDA device");
+
+  auto* P = new fct_plan_s();
+  P->opt = o;
+  std::string err;
+  fct_status s = build_host_tables(D, N, support, K, sizes, nodes, true, &P->H, &err);
+  if (s != FCT_OK) {
+    delete P;
+    return fail(s, err);
+  }
+  HostTables& H = P->H;
+  P->D = D;
+  P->K = K;
+  P->N = N;
+  P->M = H.M;
+  P->R = H.R;
+  P->sizes.assign(sizes, sizes + static_cast<size_t>(K) * D);
+  for (int64_t e = 0; e < N * D; ++e) P->dmax = std::max<int>(P->dmax, support[e]);
+  P->block_threads = o.block_threads;
+  cudaGetDevice(&P->device);
+
+  // launch shape of the solver: warp 0 of each block reduces, the other
+  // BT - 32 threads gather
+  const int BT = o.block_threads;
+  const int workers = BT - 32;
+  int L = o.coef_lanes;
+  if (L == 0) {
+    // at most 8 grid entries per lane, so one staged round of loads
+    L = 1;
+    while (L < 16 && L * 8 < K) L <<= 1;
+  }
+  DevPlan& hp = P->hp;
+  hp.N = static_cast<int32_t>(N);
+  hp.R = static_cast<int32_t>(H.R);
+  hp.K = K;
+  hp.D = D;
+  hp.M = H.M;
+  hp.npass = H.npass;
+  hp.coef_lanes = L;
+  hp.workers = workers;
+  hp.coefs_per_chunk = workers / L;
+  hp.n_coef_chunks = static_cast<int32_t>((N + hp.coefs_per_chunk - 1) / hp.coefs_per_chunk);
+  hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
+  device_row_order(&H);
+  std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
+  row_units(H, workers, &ru_first, &ru_lanes);
+  final_pass_rows(H, &rowbase, &rowk);
+  hp.n_row_units = static_cast<int32_t>(ru_lanes.size());
+  hp.n_mats = static_cast<int32_t>(H.dct_mats.size());
+  hp.mats_smem = H.dct_mats.size() * sizeof(double) <= 32768 ? hp.n_mats : 0;
+  P->ru_first = ru_first;
+  P->rowptr_h = H.rowptr;
+
+  // one device allocation, carved in 256-byte aligned pieces
+  const int64_t KN = static_cast<int64_t>(K) * N;
+  const int64_t nnodes = static_cast<int64_t>(H.node_pos.size());
+  struct Piece {
+    void** dst;
+    size_t bytes;
+  };
+  std::vector<Piece> pieces;
+  auto add = [&](void* dst, size_t bytes) { pieces.push_back({reinterpret_cast<void**>(dst), bytes}); };
+  int32_t *d_pass, *d_rowptr, *d_col, *d_crow, *d_rowbase, *d_rowk, *d_rowgrid, *d_ru_first, *d_ru_lanes;
+  DctChunk* d_chunks;
+  GridFinal* d_gfinal;
+  double *d_mats, *d_wcsr, *d_wcm;
+  float *d_wcsr32, *d_wcm32;
+  add(&P->dp, sizeof(DevPlan));
+  add(&P->ls, sizeof(LaunchState));
+  add(&P->drep, sizeof(fct_report));
+  add(&d_pass, sizeof(int32_t) * H.pass_chunk_off.size());
+  add(&d_chunks, sizeof(DctChunk) * H.dct_chunks.size());
+  add(&d_mats, sizeof(double) * H.dct_mats.size());
+  add(&d_gfinal, sizeof(GridFinal) * K);
+  add(&d_rowbase, sizeof(int32_t) * H.R);
+  add(&d_rowk, sizeof(int32_t) * H.R);
+  add(&d_rowgrid, sizeof(int32_t) * H.R);
+  add(&d_ru_first, sizeof(int32_t) * ru_first.size());
+  add(&d_ru_lanes, sizeof(int32_t) * ru_lanes.size());
+  add(&d_rowptr, sizeof(int32_t) * (H.R + 1));
+  add(&d_col, sizeof(int32_t) * KN);
+  add(&d_wcsr, sizeof(double) * KN);
+  add(&d_wcsr32, sizeof(float) * KN);
+  add(&d_crow, sizeof(int32_t) * KN);
+  add(&d_wcm, sizeof(double) * KN);
+  add(&d_wcm32, sizeof(float) * KN);
+  add(&hp.y0, sizeof(double) * std::max<int64_t>(H.M, 1));
+  add(&hp.y1, sizeof(double) * std::max<int64_t>(H.M, 1));
+  add(&hp.b, sizeof(double) * H.R);
+  add(&hp.rres, sizeof(double) * H.R);
+  add(&hp.q, sizeof(double) * H.R);
+  add(&hp.sp, sizeof(double2) * N);
+  add(&hp.part_r, sizeof(double) * hp.n_row_units);
+  add(&hp.part_c, sizeof(double) * hp.n_coef_chunks);
+  add(&hp.q32, sizeof(float) * H.R);
+  add(&hp.sp32, sizeof(float2) * N);
+  add(&hp.dx32, sizeof(float) * N);
+  add(&P->d_sizes, sizeof(int32_t) * K * D);
+  add(&P->d_offsets, sizeof(int64_t) * (K + 1));
+  add(&P->d_node_off, sizeof(int32_t) * K * D);
+  add(&P->d_node_pos, sizeof(double) * nnodes);
+  add(&P->d_support, sizeof(uint16_t) * N * D);
+  add(&P->d_ttab, sizeof(double) * nnodes * (P->dmax + 1));
+  size_t total = 0;
+  for (auto& pc : pieces) total += align256(std::max<size_t>(pc.bytes, 1));
+  cudaError_t e = cudaMalloc(&P->dmem, total);
+  if (e != cudaSuccess) {
+    delete P;
+    return cuda_fail(e, "cudaMalloc(plan)");
+  }
+  P->dbytes = total;
+  {
+    size_t off = 0;
+    for (auto& pc : pieces) {
+      *pc.dst = P->dmem + off;
+      off += align256(std::max<size_t>(pc.bytes, 1));
+    }
+  }
+  hp.pass_chunk_off = d_pass;
+  hp.dct_chunks = d_chunks;
+  hp.dct_mats = d_mats;
+  hp.gfinal = d_gfinal;
+  hp.rowbase = d_rowbase;
+  hp.rowk = d_rowk;
+  hp.rowgrid = d_rowgrid;
+  hp.ru_first = d_ru_first;
+  hp.ru_lanes = d_ru_lanes;
+  hp.rowptr = d_rowptr;
+  hp.col = d_col;
+  hp.wcsr = d_wcsr;
+  hp.wcsr32 = d_wcsr32;
+  hp.crow = d_crow;
+  hp.wcm = d_wcm;
+  hp.wcm32 = d_wcm32;
+
+  std::vector<float> w32(KN), wc32(KN);
+  for (int64_t i = 0; i < KN; ++i) {
+    w32[i] = static_cast<float>(H.wcsr[i]);
+    wc32[i] = static_cast<float>(H.weight[i]);
+  }
+  auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
+    if (bytes == 0) return cudaSuccess;
+    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+  };
+  cudaError_t ue = cudaSuccess;
+  auto chk = [&](cudaError_t x) {
+    if (ue == cudaSuccess) ue = x;
+  };
+  chk(cudaMemset(P->ls, 0, sizeof(LaunchState)));
+  chk(up(d_pass, H.pass_chunk_off.data(), sizeof(int32_t) * H.pass_chunk_off.size()));
+  chk(up(d_chunks, H.dct_chunks.data(), sizeof(DctChunk) * H.dct_chunks.size()));
+  chk(up(d_mats, H.dct_mats.data(), sizeof(double) * H.dct_mats.size()));
+  chk(up(d_gfinal, H.gfinal.data(), sizeof(GridFinal) * K));
+  chk(up(d_rowbase, rowbase.data(), sizeof(int32_t) * H.R));
+  chk(up(d_rowk, rowk.data(), sizeof(int32_t) * H.R));
+  chk(up(d_rowgrid, H.rowgrid.data(), sizeof(int32_t) * H.R));
+  chk(up(d_ru_first, ru_first.data(), sizeof(int32_t) * ru_first.size()));
+  chk(up(d_ru_lanes, ru_lanes.data(), sizeof(int32_t) * ru_lanes.size()));
+  chk(up(d_rowptr, H.rowptr.data(), sizeof(int32_t) * (H.R + 1)));
+  chk(up(d_col, H.col.data(), sizeof(int32_t) * KN));
+  chk(up(d_wcsr, H.wcsr.data(), sizeof(double) * KN));
+  chk(up(d_wcsr32, w32.data(), sizeof(float) * KN));
+  // coefficient-major row table holds global rows
+  chk(up(d_crow, H.crow.data(), sizeof(int32_t) * KN));
+  chk(up(d_wcm, H.weight.data(), sizeof(double) * KN));
+  chk(up(d_wcm32, wc32.data(), sizeof(float) * KN));
+  chk(up(P->d_sizes, sizes, sizeof(int32_t) * K * D));
+  chk(up(P->d_offsets, H.offsets.data(), sizeof(int64_t) * (K + 1)));
+  chk(up(P->d_node_off, H.node_off.data(), sizeof(int32_t) * K * D));
+  chk(up(P->d_node_pos, H.node_pos.data(), sizeof(double) * nnodes));
+  chk(up(P->d_support, support, sizeof(uint16_t) * N * D));
+  s = FCT_OK;
+  if (ue == cudaSuccess) s = choose_shape(P);
+  if (ue == cudaSuccess && s == FCT_OK) chk(up(P->dp, &hp, sizeof(DevPlan)));
+  if (ue == cudaSuccess && s == FCT_OK && nnodes > 0) {
+    cheb_table_kernel<<<static_cast<unsigned>((nnodes + 127) / 128), 128>>>(P->d_node_pos, static_cast<int>(nnodes),
+                                                                           P->dmax, P->d_ttab);
+    chk(cudaGetLastError());
+    chk(cudaDeviceSynchronize());
+  }
+  if (ue != cudaSuccess || s != FCT_OK) {
+    cudaFree(P->dmem);
+    delete P;
+    return ue != cudaSuccess ? cuda_fail(ue, "plan upload") : s;
+  }
+  // free the host copies that are no longer needed
+  H.bin.clear(); H.bin.shrink_to_fit();
+  H.col.clear(); H.col.shrink_to_fit();
+  H.wcsr.clear(); H.wcsr.shrink_to_fit();
+  H.weight.clear(); H.weight.shrink_to_fit();
+  H.crow.clear(); H.crow.shrink_to_fit();
+  *out = P;
+  return FCT_OK;
+}
+
+fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
+  if (!P || !info) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  info->N = P->N;
+  info->M = P->M;
+  info->R = P->R;
+  info->nnz = static_cast<int64_t>(P->K) * P->N;
+  info->D = P->D;
+  info->K = P->K;
+  info->passes = P->H.npass;
+  info->grid_blocks = P->grid_blocks;
+  info->block_threads = P->block_threads;
+  info->coef_lanes = P->hp.coef_lanes;
+  info->device_bytes = static_cast<int64_t>(P->dbytes);
+  return FCT_OK;
+}
+
+fct_status fct_grid_offsets(fct_plan P, int64_t* offsets) {
+  if (!P || !offsets) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(offsets, P->H.offsets.data(), sizeof(int64_t) * (P->K + 1));
+  return FCT_OK;
+}
+
+fct_status fct_sample(fct_plan P, int family, const double* params, int64_t nparams, double* samples,
+                      void* stream) {
+  if (!P || !params || !samples) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  int64_t need = 0;
+  switch (family) {
+    case FCT_FAMILY_POLY: need = P->N; break;
+    case FCT_FAMILY_GAUSSCOS: need = 2 * P->D; break;
+    case FCT_FAMILY_RATIONAL: need = P->D; break;
+    case FCT_FAMILY_POLY_GAUSSCOS: need = 2 * P->D + P->N; break;
+    default: return fail(FCT_ERR_INVALID_ARG, "unknown family");
+  }
+  if (nparams != need) return fail(FCT_ERR_INVALID_ARG, "params length does not match the family");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (nparams > P->params_cap) {
+    if (P->d_params) {
+      FCT_CUDA(cudaStreamSynchronize(st));
+      cudaFree(P->d_params);
+      P->d_params = nullptr;
+    }
+    FCT_CUDA(cudaMalloc(&P->d_params, sizeof(double) * nparams));
+    P->params_cap = nparams;
+  }
+  FCT_CUDA(cudaMemcpyAsync(P->d_params, params, sizeof(double) * nparams, cudaMemcpyHostToDevice, st));
+  FCT_CUDA(cudaStreamSynchronize(st));  // params are host memory the caller may reuse
+  SampleArgs a;
+  a.sizes = P->d_sizes;
+  a.offsets = P->d_offsets;
+  a.node_off = P->d_node_off;
+  a.node_pos = P->d_node_pos;
+  a.ttab = P->d_ttab;
+  a.support = P->d_support;
+  a.params = P->d_params;
+  a.out = samples;
+  a.M = P->M;
+  a.K = P->K;
+  a.D = P->D;
+  a.N = static_cast<int>(P->N);
+  a.family = family;
+  a.dmax = P->dmax;
+  const int bt = 128;
+  sample_kernel<<<static_cast<unsigned>((P->M + bt - 1) / bt), bt, 0, st>>>(a);
+  FCT_CUDA(cudaGetLastError());
+  return FCT_OK;
+}
+
+static fct_status read_report(fct_plan P, fct_report* dsrc, cudaStream_t st, fct_report* rep, int n = 1) {
+  FCT_CUDA(cudaMemcpyAsync(rep, dsrc, sizeof(fct_report) * n, cudaMemcpyDeviceToHost, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
+  int err = 0;
+  FCT_CUDA(cudaMemcpy(&err, &P->ls->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err != 0) {
+    P->dirty_state = true;
+    for (int i = 0; i < n; ++i) rep[i].status = err;
+    return fail(static_cast<fct_status>(err), "device-side wait expired in the solver");
+  }
+  fct_status worst = FCT_OK;
+  for (int i = 0; i < n; ++i)
+    if (rep[i].status != FCT_OK && worst == FCT_OK) worst = static_cast<fct_status>(rep[i].status);
+  if (worst != FCT_OK) return fail(worst, std::string("solver finished with ") + fct_status_string(worst));
+  return FCT_OK;
+}
+
+fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* stream, fct_report* rep) {
+  if (!P || !samples || !coeffs) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SolveArgs a{};
+  a.single = make_job(P, samples, coeffs, P->drep);
+  a.jobs = nullptr;
+  a.njobs = 1;
+  a.team_blocks = P->grid_blocks;
+  a.ls = P->ls;
+  a.timeout_ns = timeout_ns(P);
+  a.smem_bytes = P->smem_bytes;
+  fct_status s = launch_solve(P, a, P->grid_blocks, st);
+  if (s != FCT_OK) return s;
+  if (rep) return read_report(P, P->drep, st, rep);
+  return FCT_OK;
+}
+
+fct_status fct_plan_last_report(fct_plan P, void* stream, fct_report* rep) {
+  if (!P || !rep) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  return read_report(P, P->drep, static_cast<cudaStream_t>(stream), rep);
+}
+
+fct_status fct_execute_host(fct_plan P, const double* samples_host, double* coeffs_host, void* stream,
+                            fct_report* rep) {
+  if (!P || !samples_host || !coeffs_host) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!P->d_stage_in) {
+    FCT_CUDA(cudaMalloc(&P->d_stage_in, sizeof(double) * P->M));
+    FCT_CUDA(cudaMalloc(&P->d_stage_out, sizeof(double) * P->N));
+  }
+  FCT_CUDA(cudaMemcpyAsync(P->d_stage_in, samples_host, sizeof(double) * P->M, cudaMemcpyHostToDevice, st));
+  fct_status s = fct_execute(P, P->d_stage_in, P->d_stage_out, stream, nullptr);
+  if (s != FCT_OK) return s;
+  FCT_CUDA(cudaMemcpyAsync(coeffs_host, P->d_stage_out, sizeof(double) * P->N, cudaMemcpyDeviceToHost, st));
+  if (rep) return read_report(P, P->drep, st, rep);
+  FCT_CUDA(cudaStreamSynchronize(st));
+  return FCT_OK;
+}
+
+fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* samples, double* const* coeffs,
+                             int team_blocks, void* stream, fct_report* reps) {
+  if (B < 1 || !plans || !samples || !coeffs) return fail(FCT_ERR_INVALID_ARG, "bad batch arguments");
+  for (int i = 0; i < B; ++i) {
+    if (!plans[i] || !samples[i] || !coeffs[i]) return fail(FCT_ERR_INVALID_ARG, "NULL plan or buffer in batch");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(FCT_ERR_INVALID_ARG, "a plan appears twice in one batch");
+    if (plans[i]->block_threads != plans[0]->block_threads)
+      return fail(FCT_ERR_INVALID_ARG, "all plans of a batch must use the same block_threads");
+  }
+  fct_plan P0 = plans[0];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the batch's job array and reports live in plan 0's memory
+  if (P0->djobs_cap < B) {
+    if (P0->djobs) {
+      FCT_CUDA(cudaStreamSynchronize(st));
+      cudaFree(P0->djobs);
+    }
+    FCT_CUDA(cudaMalloc(&P0->djobs, (sizeof(SolveJob) + sizeof(fct_report)) * B));
+    P0->djobs_cap = B;
+  }
+  fct_report* dreps = reinterpret_cast<fct_report*>(P0->djobs + P0->djobs_cap);
+  std::vector<SolveJob> jobs(B);
+  for (int i = 0; i < B; ++i) jobs[i] = make_job(plans[i], samples[i], coeffs[i], dreps + i);
+  FCT_CUDA(cudaMemcpyAsync(P0->djobs, jobs.data(), sizeof(SolveJob) * B, cudaMemcpyHostToDevice, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
+  int G = team_blocks;
+  if (G <= 0) {
+    int units = 0;
+    for (int i = 0; i < B; ++i) units = std::max(units, plans[i]->grid_blocks);
+    G = std::max(1, std::min(units, P0->max_coresident / std::max(1, std::min(B, 16))));
+  }
+  G = std::min(G, P0->max_coresident);
+  int teams = std::min(std::max(1, P0->max_coresident / G), std::min(B, kMaxTeams));
+  SolveArgs a{};
+  a.jobs = P0->djobs;
+  a.njobs = B;
+  a.team_blocks = G;
+  a.ls = P0->ls;
+  a.timeout_ns = timeout_ns(P0);
+  size_t need = 0;
+  for (int i = 0; i < B; ++i) need = std::max(need, team_smem_need(plans[i], G));
+  a.smem_bytes = static_cast<int>(std::min<size_t>(need, P0->smem_cap) + 15) & ~15;
+  a.smem_bytes = std::min(a.smem_bytes, P0->smem_cap);
+  fct_status s = launch_solve(P0, a, teams * G, st);
+  if (s != FCT_OK) return s;
+  if (reps) return read_report(P0, dreps, st, reps, B);
+  return FCT_OK;
+}
+
+fct_status fct_destroy(fct_plan P) {
+  if (!P) return FCT_OK;
+  cudaDeviceSynchronize();
+  if (P->d_params) cudaFree(P->d_params);
+  if (P->d_stage_in) cudaFree(P->d_stage_in);
+  if (P->d_stage_out) cudaFree(P->d_stage_out);
+  if (P->djobs) cudaFree(P->djobs);
+  if (P->dmem) cudaFree(P->dmem);
+  delete P;
+  return FCT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Internal structures of the GB300 sparse-FCT library (host plan builder and
+// device kernels).  Not part of the public ABI (include/fct.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "fct.h"
+
+namespace fct {
+
+constexpr int kMaxD = 255;
+constexpr int kDctChunk = 1024;        // elements of one grid per DCT work unit
+constexpr int kMaxTeams = 1024;        // teams per launch (batched execute)
+constexpr int kEntriesPerLane = 2;     // target CSR entries per thread in the A p gather
+
+// One DCT-I work unit: a contiguous element range of one grid tensor in one
+// axis pass.  Output element e (within the grid) is
+//   out[e] = sum_j C[k][j] * in[e - k*stride + j*stride],  k = (e/stride) % n.
+struct DctChunk {
+  int64_t base;            // grid's first sample in samples / y0 / y1
+  int32_t start, count;    // element range within the grid tensor
+  int32_t n, stride;       // axis length (1 = identity copy) and its stride
+  int32_t mat;             // offset of the n x n matrix in dct_mats
+  int8_t in_sel, out_sel;  // 0 = caller samples, 1 = y0, 2 = y1
+  int16_t pad;
+};
+static_assert(sizeof(DctChunk) == 32, "DctChunk layout");
+
+// Last DCT-I pass of a grid, evaluated only at its nonempty bins (fused with
+// the gather of b): b[row] = sum_j C[k][j] * in[rowbase[row] + j*stride].
+struct GridFinal {
+  int32_t n, stride, mat;
+  int32_t in_sel;          // 0 = caller samples, 1 = y0, 2 = y1
+};
+
+// Everything the solver kernel needs about one plan; lives in device memory.
+struct DevPlan {
+  int32_t N, R, K, D;
+  int64_t M;
+  int32_t npass;             // full DCT axis passes (every grid's last pass is fused into b)
+  int32_t n_row_units;       // A p gather units (adaptive lanes per row)
+  int32_t n_rowel_chunks;    // elementwise units over rows: ceil(R / workers)
+  int32_t n_coef_chunks;     // A^T q gather units: ceil(N / coefs_per_chunk)
+  int32_t coefs_per_chunk;   // = workers / coef_lanes
+  int32_t coef_lanes;        // threads per coefficient in the A^T q gather
+  int32_t workers;           // gather threads per block (block threads - 32)
+  int32_t mats_smem;         // doubles of DCT matrices to stage in shared memory (0 = read global)
+  int32_t n_mats;            // doubles in dct_mats
+  int32_t pad0;
+  // DCT
+  const int32_t* pass_chunk_off;  // [npass + 1]
+  const DctChunk* dct_chunks;
+  const double* dct_mats;
+  const GridFinal* gfinal;   // [K]
+  const int32_t* rowbase;    // [R] first input element of the row's last-pass fibre
+  const int32_t* rowk;       // [R] output index k of the row's bin on the last axis
+  const int32_t* rowgrid;    // [R] grid of the row
+  // alias tables
+  const int32_t* ru_first;   // [n_row_units] first row of each A p unit
+  const int32_t* ru_lanes;   // [n_row_units] lanes per row in the unit (power of 2 <= 32)
+  const int32_t* rowptr;     // [R+1]  CSR by bin, rows sorted by descending length
+  const int32_t* col;        // [K*N]  column of each CSR entry (m ascending in a bin)
+  const double* wcsr;        // [K*N]  entry value, CSR order
+  const float* wcsr32;       // [K*N]
+  const int32_t* crow;       // [K*N]  crow[l*N + m] = row of column m on grid l
+  const double* wcm;         // [K*N]  entry value, coefficient-major order
+  const float* wcm32;        // [K*N]
+  // FP64 workspace
+  double* y0;                // [M]
+  double* y1;                // [M]
+  double* b;                 // [R]
+  double* rres;              // [R] FP64 residual b - A x (mixed path sweeps)
+  double* q;                 // [R]
+  double2* sp;               // [N] {s, p} interleaved: one 16-byte gather per entry
+  double* part_r;            // [n_row_units]
+  double* part_c;            // [n_coef_chunks]
+  // FP32 workspace of the mixed path
+  float* q32;                // [R]
+  float2* sp32;              // [N] {s, p} of the inner FP32 solve
+  float* dx32;               // [N]
+};
+
+// One transform of a launch.
+struct SolveJob {
+  const DevPlan* plan;       // device pointer
+  const double* samples;     // device [M]
+  double* coeffs;            // device [N]
+  fct_report* report;        // device, one per job
+  int32_t precision;
+  int32_t max_iter;
+  int32_t max_refine;
+  int32_t pad;
+  double tol;
+  double inner_tol;
+};
+
+// Barrier of one team: a monotonic arrival counter (target = G x barrier
+// number) and an exit counter that lets the last block reset it.
+struct TeamBarrier {
+  unsigned int count;
+  unsigned int pad0[31];
+  unsigned int exits;
+  unsigned int pad1[31];
+};
+
+// Per-launch device state (zeroed before every launch).
+struct LaunchState {
+  unsigned int queue_head;
+  int err;
+  int pad[30];
+  int team_job[kMaxTeams];
+  TeamBarrier bars[kMaxTeams];
+};
+
+// Host-side alias tables of a plan (also exported by fct_alias_tables_host).
+// Rows are numbered grid by grid, nonempty bins in ascending bin order;
+// device_row_order() renumbers them for the solver.
+struct HostTables {
+  int D = 0, K = 0;
+  int64_t N = 0, M = 0, R = 0;
+  std::vector<int64_t> offsets;        // [K+1] sample offsets
+  std::vector<int32_t> bin;            // [K*N] full-grid bin of m on grid l
+  std::vector<int32_t> crow;           // [K*N] global compressed row
+  std::vector<double> weight;          // [K*N] coefficient-major entries
+  std::vector<int32_t> rowptr;         // [R+1]
+  std::vector<int32_t> col;            // [K*N]
+  std::vector<double> wcsr;            // [K*N]
+  std::vector<int32_t> rowsrc;         // [R] global index into y0 (offset + bin)
+  std::vector<int32_t> rowgrid;        // [R] grid of each row
+  std::vector<int32_t> row_off;        // [K+1] first row of each grid
+  // DCT: full passes (all but each grid's last), then the fused last pass
+  int npass = 0;
+  std::vector<int32_t> pass_chunk_off; // [npass+1]
+  std::vector<DctChunk> dct_chunks;
+  std::vector<double> dct_mats;
+  std::vector<GridFinal> gfinal;       // [K]
+  // sampler geometry: node positions of every grid axis
+  std::vector<int32_t> node_off;       // [K*D] offset of grid l axis i in nodes
+  std::vector<double> node_pos;
+};
+
+// Validates inputs and builds all host tables.  Returns FCT_OK or an error with
+// the message in *err.
+fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
+                             const int32_t* sizes, const double* nodes, bool with_dct,
+                             HostTables* out, std::string* err);
+
+// Renumber the rows of H for the device: stable sort by descending gather
+// lane count (see row_units), so that rows with equal lane counts are
+// contiguous and keep their ascending-bin order.
+// Rewrites rowptr, col, wcsr, rowsrc, rowgrid and crow in place.
+void device_row_order(HostTables* H);
+
+// A p gather units for `workers` threads per block: rows get
+// min(32, pow2 >= ceil(len / kEntriesPerLane)) lanes; a unit holds
+// workers / lanes consecutive rows of equal lane count.
+void row_units(const HostTables& H, int workers, std::vector<int32_t>* first, std::vector<int32_t>* lanes);
+
+// Per-row inputs of the fused last DCT pass (after device_row_order).
+void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::vector<int32_t>* rowk);
+
+// T_m(x) by the three-term recurrence.
+double cheb_T(int m, double x);
+
+// cos(pi * a / h) for integers 0 <= a, h >= 1, with the argument reduced
+// exactly (symmetry about pi/2 and pi) before one call to cos.
+double cos_pi_ratio(int64_t a, int64_t h);
+
+void set_error(const std::string& msg);
+fct_status fail(fct_status s, const std::string& msg);
+
+}  // namespace fct

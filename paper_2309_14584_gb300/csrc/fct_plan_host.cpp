@@ -1,0 +1,387 @@
+// Host-side plan construction for the GB300 sparse FCT: alias (fold) tables,
+// bin-sorted CSR, DCT-I matrices and DCT pass work units.  Pure C++: the same
+// code backs fct_plan_create and the device-free fct_alias_tables_host.
+//
+// Alias structure (Sec. 3.1-3.3 of the paper, Eq. (aliasing_matrix_nd_diff)
+// and Eq. (L-grid_A_mat)), read on Chebyshev extrema grids with a DCT-I:
+// column m of grid l's block has exactly one nonzero, in the row-major bin
+//   bin_l(m) = sum_{i: n_i >= 2} fold_{n_i}(m_i) * stride_i,
+//   fold_n(m) = r if r <= n-1 else 2(n-1) - r,  r = m mod 2(n-1),
+// with value prod_{i: n_i = 1} T_{m_i}(xi_{l,i}).  Empty bins are dropped;
+// nonempty bins of grid l become rows row_off[l] .. row_off[l+1]-1 in
+// ascending bin order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "fct_internal.h"
+
+namespace fct {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fct_status fail(fct_status s, const std::string& msg) {
+  set_error(msg);
+  return s;
+}
+
+double cheb_T(int m, double x) {
+  if (m == 0) return 1.0;
+  double t0 = 1.0, t1 = x;
+  for (int k = 1; k < m; ++k) {
+    double t2 = 2.0 * x * t1 - t0;
+    t0 = t1;
+    t1 = t2;
+  }
+  return t1;
+}
+
+double cos_pi_ratio(int64_t a, int64_t h) {
+  // cos(pi a / h): reduce a to [0, 2h), then to [0, h] by cos(2pi - t) = cos t,
+  // then to [0, h/2] by cos(pi - t) = -cos t.
+  int64_t p = 2 * h;
+  a %= p;
+  if (a < 0) a += p;
+  if (a > h) a = p - a;
+  double sign = 1.0;
+  if (2 * a > h) {
+    a = h - a;
+    sign = -1.0;
+  }
+  if (2 * a == h) return 0.0;
+  if (a == 0) return sign;
+  return sign * std::cos(M_PI * static_cast<double>(a) / static_cast<double>(h));
+}
+
+static inline int64_t fold_index(int64_t m, int64_t n) {
+  const int64_t period = 2 * (n - 1);
+  const int64_t r = m % period;
+  return r <= n - 1 ? r : period - r;
+}
+
+fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
+                             const int32_t* sizes, const double* nodes, bool with_dct,
+                             HostTables* out, std::string* err) {
+  auto bad = [&](const std::string& m) {
+    *err = m;
+    return FCT_ERR_INVALID_ARG;
+  };
+  if (D < 1 || D > kMaxD) return bad("D must be in [1, 255]");
+  if (N < 1) return bad("N must be >= 1");
+  if (K < 1) return bad("K must be >= 1");
+  if (!support || !sizes) return bad("support and sizes must not be NULL");
+  if (static_cast<int64_t>(K) * N >= (int64_t(1) << 31)) return bad("K*N must be below 2^31");
+
+  HostTables& H = *out;
+  H = HostTables();
+  H.D = D;
+  H.K = K;
+  H.N = N;
+  H.offsets.assign(K + 1, 0);
+  for (int l = 0; l < K; ++l) {
+    int64_t T = 1;
+    for (int i = 0; i < D; ++i) {
+      const int32_t n = sizes[l * D + i];
+      if (n < 1) return bad("grid " + std::to_string(l) + " axis " + std::to_string(i) + ": size < 1");
+      T *= n;
+      if (T >= (int64_t(1) << 31)) return bad("grid " + std::to_string(l) + " has 2^31 or more points");
+      if (n == 1 && nodes) {
+        const double xi = nodes[l * D + i];
+        if (!(xi >= -1.0 && xi <= 1.0)) return bad("single-point node outside [-1, 1]");
+      }
+    }
+    H.offsets[l + 1] = H.offsets[l] + T;
+    if (H.offsets[l + 1] >= (int64_t(1) << 31)) return bad("total sample count M must be below 2^31");
+  }
+  H.M = H.offsets[K];
+
+  const int64_t KN = static_cast<int64_t>(K) * N;
+  H.bin.resize(KN);
+  H.crow.resize(KN);
+  H.weight.resize(KN);
+  H.col.resize(KN);
+  H.wcsr.resize(KN);
+  H.row_off.assign(K + 1, 0);
+  H.rowptr.clear();
+  H.rowsrc.clear();
+  H.rowgrid.clear();
+  H.rowptr.push_back(0);
+
+  std::vector<int64_t> stride(D);
+  std::vector<int32_t> count;
+  std::vector<int32_t> comp;
+  for (int l = 0; l < K; ++l) {
+    const int32_t* sz = sizes + static_cast<int64_t>(l) * D;
+    stride[D - 1] = 1;
+    for (int i = D - 2; i >= 0; --i) stride[i] = stride[i + 1] * sz[i + 1];
+    const int64_t T = H.offsets[l + 1] - H.offsets[l];
+    int32_t* bl = H.bin.data() + static_cast<int64_t>(l) * N;
+    double* wl = H.weight.data() + static_cast<int64_t>(l) * N;
+    for (int64_t m = 0; m < N; ++m) {
+      const uint16_t* mi = support + m * D;
+      int64_t bidx = 0;
+      double w = 1.0;
+      for (int i = 0; i < D; ++i) {
+        const int32_t n = sz[i];
+        if (n >= 2) {
+          bidx += fold_index(mi[i], n) * stride[i];
+        } else if (mi[i] != 0) {
+          const double xi = nodes ? nodes[l * D + i] : 1.0;
+          w *= cheb_T(mi[i], xi);
+        }
+      }
+      bl[m] = static_cast<int32_t>(bidx);
+      wl[m] = w;
+    }
+    // counting sort by bin (stable in m): nonempty bins in ascending order
+    count.assign(static_cast<size_t>(T) + 1, 0);
+    for (int64_t m = 0; m < N; ++m) count[bl[m] + 1]++;
+    comp.assign(static_cast<size_t>(T), -1);
+    const int32_t row0 = static_cast<int32_t>(H.rowsrc.size());
+    int32_t nrows = 0;
+    for (int64_t t = 0; t < T; ++t) {
+      if (count[t + 1] > 0) {
+        comp[t] = row0 + nrows++;
+        H.rowsrc.push_back(static_cast<int32_t>(H.offsets[l] + t));
+        H.rowgrid.push_back(l);
+        H.rowptr.push_back(H.rowptr.back() + count[t + 1]);
+      }
+    }
+    // scatter columns into CSR, m ascending within each bin
+    std::vector<int32_t> fill(nrows, 0);
+    for (int64_t m = 0; m < N; ++m) {
+      const int32_t r = comp[bl[m]];
+      H.crow[static_cast<int64_t>(l) * N + m] = r;
+      const int32_t pos = H.rowptr[r] + fill[r - row0]++;
+      H.col[pos] = static_cast<int32_t>(m);
+      H.wcsr[pos] = wl[m];
+    }
+    H.row_off[l + 1] = row0 + nrows;
+  }
+  H.R = static_cast<int64_t>(H.rowsrc.size());
+
+  // node positions of every grid axis (used by the sampler)
+  H.node_off.resize(static_cast<size_t>(K) * D);
+  H.node_pos.clear();
+  for (int l = 0; l < K; ++l) {
+    for (int i = 0; i < D; ++i) {
+      const int32_t n = sizes[l * D + i];
+      H.node_off[l * D + i] = static_cast<int32_t>(H.node_pos.size());
+      if (n == 1) {
+        H.node_pos.push_back(nodes ? nodes[l * D + i] : 1.0);
+      } else {
+        for (int j = 0; j < n; ++j) H.node_pos.push_back(cos_pi_ratio(j, n - 1));
+      }
+    }
+  }
+
+  if (!with_dct) return FCT_OK;
+
+  // DCT-I interpolation matrices, one per distinct axis length:
+  //   C[k][j] = (2 e_k/(n-1)) e_j cos(pi (j k mod 2(n-1))/(n-1)),  e = 1/2 at the ends.
+  std::vector<int32_t> mat_of(1, -1);
+  auto matrix_for = [&](int32_t n) -> int32_t {
+    if (static_cast<int32_t>(mat_of.size()) <= n) mat_of.resize(n + 1, -1);
+    if (mat_of[n] >= 0) return mat_of[n];
+    const int32_t off = static_cast<int32_t>(H.dct_mats.size());
+    if (n == 1) {
+      H.dct_mats.push_back(1.0);
+    } else {
+      const int64_t h = n - 1;
+      for (int k = 0; k < n; ++k) {
+        const double ek = (k == 0 || k == n - 1) ? 0.5 : 1.0;
+        for (int j = 0; j < n; ++j) {
+          const double ej = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+          H.dct_mats.push_back((2.0 * ek / static_cast<double>(h)) * ej *
+                               cos_pi_ratio((static_cast<int64_t>(j) * k) % (2 * h), h));
+        }
+      }
+    }
+    mat_of[n] = off;
+    return off;
+  };
+
+  // Active axes of every grid, outermost first.  Every axis but the last is a
+  // full pass over the grid (ping-pong y0 / y1); the last is evaluated only at
+  // the nonempty bins, fused with the gather of b.  A grid with no active axis
+  // gets an identity "axis" (n = 1) as its last pass.
+  std::vector<std::vector<int>> active(K);
+  int npass = 0;
+  H.gfinal.assign(K, GridFinal{});
+  for (int l = 0; l < K; ++l) {
+    for (int i = 0; i < D; ++i)
+      if (sizes[l * D + i] >= 2) active[l].push_back(i);
+    const int A = static_cast<int>(active[l].size());
+    npass = std::max(npass, A - 1);
+    GridFinal g{};
+    if (A == 0) {
+      g.n = 1;
+      g.stride = 1;
+      g.mat = matrix_for(1);
+      g.in_sel = 0;
+    } else {
+      const int axis = active[l][A - 1];
+      g.n = sizes[l * D + axis];
+      int64_t st = 1;
+      for (int i = axis + 1; i < D; ++i) st *= sizes[l * D + i];
+      g.stride = static_cast<int32_t>(st);
+      g.mat = matrix_for(g.n);
+      g.in_sel = A == 1 ? 0 : (((A - 2) & 1) ? 2 : 1);
+    }
+    H.gfinal[l] = g;
+  }
+  H.npass = npass;
+  H.pass_chunk_off.assign(1, 0);
+  for (int p = 0; p < npass; ++p) {
+    for (int l = 0; l < K; ++l) {
+      const int A = static_cast<int>(active[l].size());
+      if (p >= A - 1) continue;
+      const int axis = active[l][p];
+      const int32_t n = sizes[l * D + axis];
+      int64_t st = 1;
+      for (int i = axis + 1; i < D; ++i) st *= sizes[l * D + i];
+      const int32_t mat = matrix_for(n);
+      const int8_t out_sel = static_cast<int8_t>((p & 1) ? 2 : 1);
+      const int8_t in_sel = p == 0 ? 0 : static_cast<int8_t>(((p - 1) & 1) ? 2 : 1);
+      const int64_t T = H.offsets[l + 1] - H.offsets[l];
+      for (int64_t e0 = 0; e0 < T; e0 += kDctChunk) {
+        DctChunk c{};
+        c.base = H.offsets[l];
+        c.start = static_cast<int32_t>(e0);
+        c.count = static_cast<int32_t>(std::min<int64_t>(kDctChunk, T - e0));
+        c.n = n;
+        c.stride = static_cast<int32_t>(st);
+        c.mat = mat;
+        c.in_sel = in_sel;
+        c.out_sel = out_sel;
+        H.dct_chunks.push_back(c);
+      }
+    }
+    H.pass_chunk_off.push_back(static_cast<int32_t>(H.dct_chunks.size()));
+  }
+  return FCT_OK;
+}
+
+static int lanes_for(int32_t len);
+
+void device_row_order(HostTables* Hp) {
+  HostTables& H = *Hp;
+  const int64_t R = H.R;
+  std::vector<int32_t> order(R);
+  for (int64_t r = 0; r < R; ++r) order[r] = static_cast<int32_t>(r);
+  // stable sort by gather lane class only: rows keep their bin order within a
+  // class, which keeps neighbouring coefficients' rows close together
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    return lanes_for(H.rowptr[a + 1] - H.rowptr[a]) > lanes_for(H.rowptr[b + 1] - H.rowptr[b]);
+  });
+  std::vector<int32_t> inv(R), rowptr(R + 1), col(H.col.size()), rowsrc(R), rowgrid(R);
+  std::vector<double> wcsr(H.wcsr.size());
+  rowptr[0] = 0;
+  for (int64_t nr = 0; nr < R; ++nr) {
+    const int32_t r = order[nr];
+    inv[r] = static_cast<int32_t>(nr);
+    const int32_t len = H.rowptr[r + 1] - H.rowptr[r];
+    rowptr[nr + 1] = rowptr[nr] + len;
+    std::copy(H.col.begin() + H.rowptr[r], H.col.begin() + H.rowptr[r + 1], col.begin() + rowptr[nr]);
+    std::copy(H.wcsr.begin() + H.rowptr[r], H.wcsr.begin() + H.rowptr[r + 1], wcsr.begin() + rowptr[nr]);
+    rowsrc[nr] = H.rowsrc[r];
+    rowgrid[nr] = H.rowgrid[r];
+  }
+  for (auto& c : H.crow) c = inv[c];
+  H.rowptr.swap(rowptr);
+  H.col.swap(col);
+  H.wcsr.swap(wcsr);
+  H.rowsrc.swap(rowsrc);
+  H.rowgrid.swap(rowgrid);
+}
+
+static int lanes_for(int32_t len) {
+  int lanes = 1;
+  while (lanes < 32 && lanes * kEntriesPerLane < len) lanes <<= 1;
+  return lanes;
+}
+
+void row_units(const HostTables& H, int workers, std::vector<int32_t>* first, std::vector<int32_t>* lanes) {
+  first->clear();
+  lanes->clear();
+  int64_t r = 0;
+  while (r < H.R) {
+    const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r]);
+    const int per = workers / lc;
+    int64_t e = r;
+    // rows are sorted by descending length, so equal lane counts are contiguous
+    while (e < H.R && e - r < per && lanes_for(H.rowptr[e + 1] - H.rowptr[e]) == lc) ++e;
+    first->push_back(static_cast<int32_t>(r));
+    lanes->push_back(lc);
+    r = e;
+  }
+  first->push_back(static_cast<int32_t>(H.R));  // sentinel: end of the last unit
+}
+
+void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::vector<int32_t>* rowk) {
+  rowbase->resize(H.R);
+  rowk->resize(H.R);
+  for (int64_t r = 0; r < H.R; ++r) {
+    const int l = H.rowgrid[r];
+    const GridFinal& g = H.gfinal[l];
+    const int64_t bin = H.rowsrc[r] - H.offsets[l];
+    const int64_t k = (bin / g.stride) % g.n;
+    (*rowbase)[r] = static_cast<int32_t>(H.offsets[l] + bin - k * g.stride);
+    (*rowk)[r] = static_cast<int32_t>(k);
+  }
+}
+
+}  // namespace fct
+
+extern "C" {
+
+const char* fct_last_error(void) { return fct::g_last_error.c_str(); }
+
+const char* fct_status_string(int s) {
+  switch (s) {
+    case FCT_OK: return "FCT_OK";
+    case FCT_ERR_INVALID_ARG: return "FCT_ERR_INVALID_ARG";
+    case FCT_ERR_RANK: return "FCT_ERR_RANK";
+    case FCT_ERR_NOCONV: return "FCT_ERR_NOCONV";
+    case FCT_ERR_TIMEOUT: return "FCT_ERR_TIMEOUT";
+    case FCT_ERR_OOM: return "FCT_ERR_OOM";
+    case FCT_ERR_NONFINITE: return "FCT_ERR_NONFINITE";
+    case FCT_ERR_CUDA: return "FCT_ERR_CUDA";
+    case FCT_ERR_NO_DEVICE: return "FCT_ERR_NO_DEVICE";
+    default: return "FCT_ERR_UNKNOWN";
+  }
+}
+
+void fct_default_options(fct_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = FCT_FP64;
+  opt->tol = 1e-13;
+  opt->max_iter = 20000;
+  opt->inner_tol = 1e-6;
+  opt->max_refine = 6;
+  opt->block_threads = 0;
+  opt->max_blocks = 0;
+  opt->coef_lanes = 0;
+  opt->timeout_s = 4.0;
+}
+
+fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,
+                                 const int32_t* sizes, const double* nodes, int32_t* bin,
+                                 int32_t* crow, double* weight, int64_t* R_out) {
+  fct::HostTables H;
+  std::string err;
+  fct_status s = fct::build_host_tables(D, N, support, K, sizes, nodes, false, &H, &err);
+  if (s != FCT_OK) return fct::fail(s, err);
+  const size_t KN = static_cast<size_t>(K) * static_cast<size_t>(N);
+  if (bin) std::memcpy(bin, H.bin.data(), KN * sizeof(int32_t));
+  if (crow) std::memcpy(crow, H.crow.data(), KN * sizeof(int32_t));
+  if (weight) std::memcpy(weight, H.weight.data(), KN * sizeof(double));
+  if (R_out) *R_out = H.R;
+  return FCT_OK;
+}
+
+}  // extern "C"

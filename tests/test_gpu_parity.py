@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Tolerances: the FP64 path must match the oracle's least-squares solution to
+1e-11 relative l2 error, the mixed path (FP32 inner solves, FP64 refinement)
+to 1e-10; integer alias tables bit-exactly (test_capi_host.py); samples to
+1e-13 absolute (O(1) values, device vs host transcendental functions).
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_2309_14584_gb300 as F
+import workloads as W
+from oracle import fct_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+TOL_MIXED = 1e-10
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_run(w, samples_np=None, **opts):
+    plan = F.Plan(w.support, w.sizes, w.nodes, **opts)
+    samples = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    if samples_np is None:
+        plan.sample(w.family, w.params, samples)
+    else:
+        samples.copy_(torch.from_numpy(np.ascontiguousarray(samples_np)))
+    coeffs = torch.full((plan.N,), float("nan"), dtype=torch.float64, device="cuda")
+    rep = plan.execute(samples, coeffs)
+    torch.cuda.synchronize()
+    out = coeffs.cpu().numpy()
+    s = samples.cpu().numpy()
+    plan.close()
+    return out, s, rep
+
+
+SMALL = [
+    # name, seed, D, d, K, lo, hi, family
+    ("D1_poly", 21, 1, 12, 5, 2, 9, W.FAMILY_POLY),
+    ("D2_gc", 41, 2, 9, 5, 3, 12, W.FAMILY_GAUSSCOS),
+    ("D3_rat", 42, 3, 6, 9, 1, 7, W.FAMILY_RATIONAL),
+    ("D4_gc", 43, 4, 5, 12, 1, 6, W.FAMILY_GAUSSCOS),
+    ("D4_polygc", 44, 4, 4, 12, 1, 5, W.FAMILY_POLY_GAUSSCOS),
+    ("D5_rat", 45, 5, 4, 15, 1, 5, W.FAMILY_RATIONAL),
+]
+
+
+def _small(case):
+    name, seed, D, d, K, lo, hi, fam = case
+    return W.make_workload(name, seed, D, d, K, lo, hi, fam)
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
+def test_sampler_matches_oracle(case):
+    w = _small(case)
+    _, s_gpu, _ = gpu_run(w)
+    s_ref = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    assert s_gpu.shape == s_ref.shape
+    assert np.max(np.abs(s_gpu - s_ref)) <= 1e-13 * max(1.0, np.max(np.abs(s_ref)))
+
+
+@pytest.mark.parametrize("case", SMALL, ids=[c[0] for c in SMALL])
+def test_fp64_small_matches_oracle(case):
+    """Same samples on both sides (the oracle's own); the solve is compared."""
+    w = _small(case)
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+    got, _, rep = gpu_run(w, samples_np=f, tol=1e-14)
+    assert rep["status"] == 0
+    assert rel(got, ref) <= TOL_FP64, (rel(got, ref), rep)
+    if w.coeffs_true is not None:
+        assert rel(got, w.coeffs_true) <= TOL_FP64
+
+
+def test_config_small_poly_recovers_and_matches_oracle():
+    w = W.config_small_poly()
+    got, s_gpu, rep = gpu_run(w, tol=1e-13)
+    ref = O.fct(w.support, w.sizes, w.nodes, O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes), "qr")
+    assert rep["status"] == 0
+    assert rel(got, ref) <= TOL_FP64
+    assert rel(got, w.coeffs_true) <= TOL_FP64
+
+
+@pytest.fixture(scope="module")
+def d6_gausscos():
+    w = W.config_d6_gausscos()
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    ref = O.fct(w.support, w.sizes, w.nodes, f, "csne")
+    return w, f, ref
+
+
+def test_d6_fp64_matches_oracle(d6_gausscos):
+    w, f, ref = d6_gausscos
+    got, s_gpu, rep = gpu_run(w, tol=1e-13)
+    assert rep["status"] == 0, rep
+    assert np.max(np.abs(s_gpu - f)) <= 1e-13
+    assert rel(got, ref) <= TOL_FP64, (rel(got, ref), rep)
+
+
+def test_d6_mixed_matches_oracle(d6_gausscos):
+    w, f, ref = d6_gausscos
+    got, _, rep = gpu_run(w, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
+    assert rep["status"] == 0, rep
+    assert rel(got, ref) <= TOL_MIXED, (rel(got, ref), rep)
+
+
+def test_d6_poly_exact_recovery():
+    """Seeded polynomial on the D=6, d=10 support sampled on the GPU: the
+    solve returns the true coefficients (consistent system)."""
+    w = W.config_d6_gausscos(family=W.FAMILY_POLY)
+    got, _, rep = gpu_run(w, tol=1e-13)
+    assert rep["status"] == 0
+    assert rel(got, w.coeffs_true) <= TOL_FP64, rel(got, w.coeffs_true)
+
+
+def test_execute_host_equals_device():
+    w = _small(SMALL[3])
+    plan = F.Plan(w.support, w.sizes, w.nodes)
+    samples = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    plan.sample(w.family, w.params, samples)
+    c_dev = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    plan.execute(samples, c_dev)
+    s_host = samples.cpu().pin_memory()
+    c_host = torch.empty(plan.N, dtype=torch.float64).pin_memory()
+    rep = plan.execute_host(s_host, c_host)
+    assert rep["status"] == 0
+    assert torch.equal(c_host, c_dev.cpu())
+    plan.close()
+
+
+def test_batch_bitwise_equals_alone():
+    ws = [_small(c) for c in SMALL[1:]] + [W.config_small_poly()]
+    plans, samples, alone = [], [], []
+    for w in ws:
+        p = F.Plan(w.support, w.sizes, w.nodes, tol=1e-13)
+        s = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(w.family, w.params, s)
+        c = torch.empty(p.N, dtype=torch.float64, device="cuda")
+        p.execute(s, c)
+        plans.append(p)
+        samples.append(s)
+        alone.append(c.clone())
+    outs = [torch.full((p.N,), float("nan"), dtype=torch.float64, device="cuda") for p in plans]
+    for team_blocks in (1, 3, 0):
+        reps = F.fct_execute_batch([p.handle for p in plans], samples, outs, team_blocks=team_blocks)
+        assert all(r["status"] == 0 for r in reps)
+        for a, o in zip(alone, outs):
+            assert torch.equal(a, o)
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.parametrize("bt,lanes,blocks", [(128, 1, 0), (256, 4, 7), (512, 16, 0), (256, 2, 1)])
+def test_launch_shapes_agree(bt, lanes, blocks):
+    w = _small(SMALL[3])
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+    got, _, rep = gpu_run(w, samples_np=f, tol=1e-14, block_threads=bt, coef_lanes=lanes, max_blocks=blocks)
+    assert rep["status"] == 0
+    assert rel(got, ref) <= TOL_FP64
+
+
+def test_edge_single_coefficient_and_single_point_grid():
+    """N = 1 (support {0}) on grids that are single points: c* = mean-free LS
+    of the constant, i.e. the average of the samples weighted as one row per grid."""
+    support = np.zeros((1, 3), dtype=np.uint16)
+    sizes = np.ones((3, 3), dtype=np.int32)
+    nodes = np.array([[0.1, 0.2, 0.3], [-0.5, 0.5, 0.0], [0.9, -0.9, 0.4]])
+    plan = F.Plan(support, sizes, nodes)
+    assert plan.M == 3
+    samples = torch.tensor([1.0, 2.0, 4.0], dtype=torch.float64, device="cuda")
+    c = torch.empty(1, dtype=torch.float64, device="cuda")
+    rep = plan.execute(samples, c)
+    assert rep["status"] == 0
+    assert abs(c.item() - 7.0 / 3.0) <= 1e-15
+    plan.close()
+
+
+def test_edge_ragged_and_one_dimensional():
+    """D = 1 with ragged grid sizes; compared with the oracle."""
+    support = np.arange(40, dtype=np.uint16)[:, None]
+    sizes = np.array([[7], [12], [5], [33], [2], [1]], dtype=np.int32)
+    nodes = np.full((6, 1), 0.37)
+    f = np.random.default_rng(3).standard_normal(int(sizes.sum()))
+    ref = O.fct(support, sizes, nodes, f, "qr")
+    plan = F.Plan(support, sizes, nodes, tol=1e-14)
+    s = torch.from_numpy(f).cuda()
+    c = torch.empty(40, dtype=torch.float64, device="cuda")
+    rep = plan.execute(s, c)
+    assert rep["status"] == 0
+    assert rel(c.cpu().numpy(), ref) <= TOL_FP64
+    plan.close()
+
+
+def test_invalid_arguments_are_rejected():
+    sup = np.zeros((4, 2), dtype=np.uint16)
+    with pytest.raises(F.FctError) as e:
+        F.Plan(sup, np.array([[0, 3]], dtype=np.int32))
+    assert e.value.status == 1
+    with pytest.raises(F.FctError):
+        F.Plan(sup, np.array([[1, 3]], dtype=np.int32), np.array([[2.0, 0.0]]))
+    with pytest.raises(F.FctError):
+        F.Plan(sup, np.array([[2, 3]], dtype=np.int32), block_threads=100)
+
+
+def test_nonfinite_samples_reported():
+    w = _small(SMALL[2])
+    plan = F.Plan(w.support, w.sizes, w.nodes)
+    s = torch.zeros(plan.M, dtype=torch.float64, device="cuda")
+    plan.sample(w.family, w.params, s)
+    s[5] = float("nan")
+    c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    with pytest.raises(F.FctError) as e:
+        plan.execute(s, c)
+    assert e.value.status == F.fct.FCT_ERR_NONFINITE
+    # the plan stays usable
+    plan.sample(w.family, w.params, s)
+    assert plan.execute(s, c)["status"] == 0
+    plan.close()
