@@ -118,7 +118,7 @@ const char* fct_status_string(int status);
  * its condition-number loop; the L-grid is an input), the DCT-I matrices and
  * the solver workspace, and upload them to the current device.
  *   D in [1, 255]; N >= 1; support host uint16[N][D] (any multi-indices);
- *   K >= 1; sizes host int32[K][D], every n >= 1, each grid's point count and
+ *   K >= 1; sizes host int32[K][D], every n in [1, 4096], each grid's point count and
  *   the total M below 2^31, K*N below 2^31; nodes host double[K][D] in [-1,1]
  *   (read where n == 1; NULL means xi = 1); opt NULL = defaults.
  * Synchronous.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_OOM, FCT_ERR_CUDA,
@@ -174,6 +174,28 @@ fct_status fct_execute_host(fct_plan plan, const double* samples_host, double* c
 fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* samples,
                              double* const* coeffs, int team_blocks, void* stream,
                              fct_report* reps);
+
+/*
+ * fct_execute without any device allocation.  No counterpart in the paper: it
+ * exists for callers that cannot allocate device memory when they solve, such
+ * as code under a memory policy that forbids cudaMalloc after start-up (a
+ * real-time loop, a fixed memory pool, a host runtime that owns the device
+ * memory).  Such a caller creates its plans ahead of time; this call then runs
+ * a plan with its solver workspace taken from one fixed 32 MiB array that the
+ * library holds in every device's memory from load until process exit.  The
+ * plan supplies only its read-only tables.  Same arguments and results as
+ * fct_execute; no cudaMalloc, cudaFree or other allocating routine is called.
+ *   - Plans whose workspace exceeds 32 MiB are rejected with
+ *     FCT_ERR_INVALID_ARG (the message gives the bytes needed).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array: calls that overlap on the GPU
+ *     (different streams, or different plans at once) race and must not be
+ *     issued.  The array keeps the last call's contents; the call clears what
+ *     must start at zero itself.
+ */
+fct_status fct_execute_noalloc(fct_plan plan, const double* samples, double* coeffs, void* stream,
+                               fct_report* rep);
 
 /* Report of the plan's last execute (waits for stream). */
 fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);

@@ -1507,3 +1507,133 @@ fct_status fct_destroy(fct_plan P) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free execute (fct_execute_noalloc)
+//
+// Some callers cannot allocate device memory when they solve: code running
+// under a memory policy that forbids cudaMalloc after start-up (real-time
+// loops, fixed memory pools, a host runtime that owns all device memory), or
+// code inside a region where an allocation would be unsafe.  They build their
+// plans ahead of time and run them through this entry point, whose solver
+// workspace lives in the fixed array below instead of in the plan.  The plan
+// still provides its read-only tables; nothing is allocated or freed here.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;  // 32 MiB per device
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};  // device address of the array, per device
+std::mutex g_noalloc_mu;
+
+// Layout of the workspace inside the array (256-byte aligned pieces).
+struct NoallocLayout {
+  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, q32, sp32, dx32, total;
+};
+
+NoallocLayout noalloc_layout(const fct_plan P) {
+  NoallocLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += align256(std::max<size_t>(bytes, 1));
+    return at;
+  };
+  const size_t M = static_cast<size_t>(std::max<int64_t>(P->M, 1)), R = static_cast<size_t>(P->R),
+               N = static_cast<size_t>(P->N);
+  L.devplan = take(sizeof(DevPlan));
+  L.report = take(sizeof(fct_report));
+  L.ls = take(sizeof(LaunchState));
+  L.y0 = take(sizeof(double) * M);
+  L.y1 = take(sizeof(double) * M);
+  L.b = take(sizeof(double) * R);
+  L.rres = take(sizeof(double) * R);
+  L.q = take(sizeof(double) * R);
+  L.sp = take(sizeof(double2) * N);
+  L.part_r = take(sizeof(double) * P->hp.n_row_units);
+  L.part_c = take(sizeof(double) * P->hp.n_coef_chunks);
+  L.q32 = take(sizeof(float) * R);
+  L.sp32 = take(sizeof(float2) * N);
+  L.dx32 = take(sizeof(float) * N);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, double* coeffs, void* stream,
+                                          fct_report* rep) {
+  if (!P || !samples || !coeffs) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  const NoallocLayout L = noalloc_layout(P);
+  if (L.total > kNoallocScratchBytes)
+    return fail(FCT_ERR_INVALID_ARG, "plan needs " + std::to_string(L.total) +
+                                         " bytes of solver workspace; fct_execute_noalloc holds at most " +
+                                         std::to_string(kNoallocScratchBytes) + " bytes (use fct_execute)");
+  int dev = 0;
+  FCT_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(FCT_ERR_INVALID_ARG, "device index out of range");
+  if (dev != P->device) return fail(FCT_ERR_INVALID_ARG, "the current device is not the plan's device");
+  void* base = nullptr;
+  {
+    // First call on this device: look up the array's device address (the host
+    // symbol is only a stand-in and must not be handed to a kernel).
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+      g_noalloc_addr[dev] = p;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  char* b = static_cast<char*>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // The plan's tables with this array's workspace.
+  DevPlan hp = P->hp;
+  hp.y0 = reinterpret_cast<double*>(b + L.y0);
+  hp.y1 = reinterpret_cast<double*>(b + L.y1);
+  hp.b = reinterpret_cast<double*>(b + L.b);
+  hp.rres = reinterpret_cast<double*>(b + L.rres);
+  hp.q = reinterpret_cast<double*>(b + L.q);
+  hp.sp = reinterpret_cast<double2*>(b + L.sp);
+  hp.part_r = reinterpret_cast<double*>(b + L.part_r);
+  hp.part_c = reinterpret_cast<double*>(b + L.part_c);
+  hp.q32 = reinterpret_cast<float*>(b + L.q32);
+  hp.sp32 = reinterpret_cast<float2*>(b + L.sp32);
+  hp.dx32 = reinterpret_cast<float*>(b + L.dx32);
+  DevPlan* dplan = reinterpret_cast<DevPlan*>(b + L.devplan);
+  fct_report* drep = reinterpret_cast<fct_report*>(b + L.report);
+  LaunchState* ls = reinterpret_cast<LaunchState*>(b + L.ls);
+  // The array keeps the previous call's contents: the launch header and the
+  // team's barrier counters must start at zero.
+  FCT_CUDA(cudaMemsetAsync(ls, 0, offsetof(LaunchState, team_job), st));
+  FCT_CUDA(cudaMemsetAsync(&ls->bars[0], 0, sizeof(TeamBarrier), st));
+  FCT_CUDA(cudaMemcpyAsync(dplan, &hp, sizeof(DevPlan), cudaMemcpyHostToDevice, st));
+  SolveArgs a{};
+  a.single = make_job(P, samples, coeffs, drep);
+  a.single.plan = dplan;
+  a.jobs = nullptr;
+  a.njobs = 1;
+  a.team_blocks = P->grid_blocks;
+  a.ls = ls;
+  a.timeout_ns = timeout_ns(P);
+  a.smem_bytes = P->smem_bytes;
+  void* kargs[] = {&a};
+  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads), dim3(P->grid_blocks),
+                                       dim3(P->block_threads), kargs, static_cast<size_t>(a.smem_bytes), st));
+  if (!rep) return FCT_OK;
+  FCT_CUDA(cudaMemcpyAsync(rep, drep, sizeof(fct_report), cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  FCT_CUDA(cudaMemcpyAsync(&err, &ls->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
+  if (err != 0) {
+    rep->status = err;
+    return fail(static_cast<fct_status>(err), "device-side wait expired in the solver");
+  }
+  if (rep->status != FCT_OK)
+    return fail(static_cast<fct_status>(rep->status),
+                std::string("solver finished with ") + fct_status_string(rep->status));
+  return FCT_OK;
+}

@@ -17,6 +17,7 @@ constexpr int kMaxD = 255;
 constexpr int kDctChunk = 1024;        // elements of one grid per DCT work unit
 constexpr int kMaxTeams = 1024;        // teams per launch (batched execute)
 constexpr int kEntriesPerLane = 2;     // target CSR entries per thread in the A p gather
+constexpr int kMaxAxis = 4096;         // longest grid axis (points) the direct DCT-I accepts
 
 // One DCT-I work unit: a contiguous element range of one grid tensor in one
 // axis pass.  Output element e (within the grid) is

@@ -86,6 +86,9 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
     for (int i = 0; i < D; ++i) {
       const int32_t n = sizes[l * D + i];
       if (n < 1) return bad("grid " + std::to_string(l) + " axis " + std::to_string(i) + ": size < 1");
+      if (n > kMaxAxis)
+        return bad("grid " + std::to_string(l) + " axis " + std::to_string(i) + ": more than " +
+                   std::to_string(kMaxAxis) + " points (the direct DCT-I holds an n x n matrix per axis length)");
       T *= n;
       if (T >= (int64_t(1) << 31)) return bad("grid " + std::to_string(l) + " has 2^31 or more points");
       if (n == 1 && nodes) {

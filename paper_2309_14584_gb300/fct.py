@@ -102,6 +102,7 @@ SIGNATURES = [
     ("fct_execute_host", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_batch", ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P]),
     ("fct_plan_last_report", ctypes.c_int, [_P, _P, ctypes.POINTER(fct_report)]),
+    ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
     ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, _P, _P, _P,
                                              ctypes.POINTER(ctypes.c_int64)]),
@@ -249,6 +250,19 @@ def fct_execute_batch(plans, samples, coeffs, team_blocks: int = 0, stream=None,
             raise FctError(st, lib().fct_last_error().decode())
         return [r.as_dict() for r in reps]
     _check(lib().fct_execute_batch(B, hp, hs, hc, team_blocks, _stream(stream), None))
+    return None
+
+
+def fct_execute_noalloc(plan: int, samples, coeffs, stream=None, report: bool = True) -> dict | None:
+    """fct_execute with the solver workspace in the library's fixed device
+    array (no device allocation; see include/fct.h)."""
+    if report:
+        rep = fct_report()
+        st = lib().fct_execute_noalloc(plan, _ptr(samples), _ptr(coeffs), _stream(stream), ctypes.byref(rep))
+        if st != FCT_OK:
+            raise FctError(st, lib().fct_last_error().decode() + f" (report {rep.as_dict()})")
+        return rep.as_dict()
+    _check(lib().fct_execute_noalloc(plan, _ptr(samples), _ptr(coeffs), _stream(stream), None))
     return None
 
 

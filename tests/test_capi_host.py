@@ -72,6 +72,9 @@ def test_alias_tables_reject_bad_input(lib):
         F.fct_alias_tables_host(sup, np.array([[0, 2]], dtype=np.int32))
     with pytest.raises(F.FctError):
         F.fct_alias_tables_host(sup, np.array([[1, 2]], dtype=np.int32), np.array([[1.5, 0.0]]))
+    with pytest.raises(F.FctError) as e:
+        F.fct_alias_tables_host(sup, np.array([[2, 5000]], dtype=np.int32))
+    assert "4096" in str(e.value)
 
 
 def test_plan_create_without_device_fails_cleanly(lib):
