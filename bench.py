@@ -203,6 +203,24 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------
+# multi-rank bookkeeping (replicas: no data-path collective)
+# ---------------------------------------------------------------------------
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """Max of a per-rank scalar over the process group (the job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(coeffs_per_step: int, steps: int, world: int, max_time_s: float) -> float:
+    """coeffs/s of the whole job: every rank solves its own stream of
+    transforms (weak scaling), divided by the slowest rank's time."""
+    return world * coeffs_per_step * steps / max_time_s
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -263,9 +281,7 @@ def run_gpu(args):
         step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
         total_s = sum(step_ms) / 1e3
         if world > 1:
-            t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_s = float(t.item())
+            total_s = max_over_ranks(total_s, device="cuda")
         rep_last = F.fct_plan_last_report(plan.handle)
         same = np.array_equal(coeffs.cpu().numpy(), c_first)
         # end to end through the host-buffer entry point (pinned memory)
@@ -298,7 +314,7 @@ def run_gpu(args):
 
     for prec, r in results.items():
         r["rel_err"] = rel(r["coeffs"], cpu["c_ref"]) if cpu is not None else None
-        r["value"] = world * w.N * args.steps / r["total_s"]
+        r["value"] = whole_job_value(w.N, args.steps, world, r["total_s"])
     valid = [p for p, r in results.items() if r["rep"]["status"] == 0 and
              (r["rel_err"] is None or r["rel_err"] <= ERR_BOUND)]
     best = max(valid or list(results), key=lambda p: results[p]["value"])

@@ -124,6 +124,54 @@ __device__ void team_exit(const Team& tm) {
   }
 }
 
+// End of a solver phase: all warps have written their per-warp partials of
+// the last nk units (wpart); warp 0 stores the unit partials part[u0 + i*G]
+// and its lane 0 arrives at and waits on the team barrier, so one block-wide
+// sync before and one after cover both the flush and the barrier.
+template <int NW>
+__device__ bool phase_end(Team& tm, const float (*wpart)[NW], float* part, int u0, int nk) {
+  __shared__ int s_ok2;
+  __syncthreads();
+  tm.epoch += 1;
+  if (threadIdx.x < 32) {
+    if (static_cast<int>(threadIdx.x) < nk) {
+      float v = 0.0f;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) v += wpart[threadIdx.x][w];
+      stcg(part + u0 + static_cast<int>(threadIdx.x) * tm.G, v);
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      if (tm.G > 1) {
+        const unsigned int target = tm.epoch * static_cast<unsigned int>(tm.G);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&tm.bar->count) : "memory");
+        if (ld_acquire_u32(&tm.bar->count) < target) {
+          const unsigned long long t0 = globaltimer_ns();
+          while (ld_acquire_u32(&tm.bar->count) < target) {
+            if (ld_volatile_i32(tm.err) != 0) {
+              ok = 0;
+              break;
+            }
+            if (globaltimer_ns() - t0 > tm.timeout_ns) {
+              atomicCAS(tm.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
+              ok = 0;
+              break;
+            }
+          }
+        }
+      } else {
+        __threadfence();
+        if (ld_volatile_i32(tm.err) != 0) ok = 0;
+      }
+      s_ok2 = ok;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  return s_ok2 != 0;
+}
+
 // Deterministic block sum; the result is valid in thread 0.
 template <int BT>
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -155,6 +203,21 @@ __device__ __forceinline__ void warp0_team_sum(const double* part, int n, double
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (threadIdx.x == 0) red[BT / 32] = v;
+}
+
+// Warp 0: FP32 sum of n chunk partials in a fixed order, left in *out (lane 0).
+__device__ __forceinline__ float warp0_team_sum_f(const float* part, int n) {
+  float v = 0.0f;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
+    float t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v += t[j];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // All threads: team sum of n partials (used outside the overlapped phases).
@@ -493,12 +556,19 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
 //   phase B: t = A^T q while warp 0 reduces |q|^2; the coefficient owner
 //            then writes {s - alpha t, s + beta p} and x + alpha p in place.
 // Workers stream through the block's units without block-wide syncs; each
-// unit's |q|^2 or |s|^2 partial is the fixed-order sum of its warps' sums,
-// so partials (and the result) do not depend on the team size.
-// V2 = {s, p} vector type (double2 / float2), XT = type of x.  Reductions are
-// FP64.  On entry sp[m].x = right-hand side, x = 0, gamma0 = |s|^2.  Stops
-// when sqrt(gamma/gamma0) <= tol, after max_iter (FCT_ERR_NOCONV) or, if
-// stall > 0, when gamma has not decreased for `stall` iterations.
+// unit's partial is the fixed-order sum of its warps' sums, so partials (and
+// the result) do not depend on the team size.
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so only the
+// vector arithmetic that needs it runs in V: the sums of squares that give
+// alpha and beta are taken relative to gamma0 and reduced in FP32 (fixed
+// order), and alpha, beta and the stopping test are computed once per block
+// by one thread and broadcast.  With V = float (the inner solve of the mixed
+// path) the loop does no FP64 arithmetic at all.
+// On entry sp[m].x = right-hand side, x = 0, gamma0 = |s|^2 (> 0).  Stops when
+// gamma <= tol^2 gamma0, after max_iter (FCT_ERR_NOCONV) or, if stall > 0,
+// when gamma has not decreased for `stall` iterations.  All threads of all
+// blocks return the same iteration count, final gamma and status.
 // ---------------------------------------------------------------------------
 constexpr int kUnitGroup = 16;  // units per flush of the per-warp partials
 
@@ -512,11 +582,13 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
                           int* iters_out, double* gamma_out, int* status_out, double* red) {
   using V2 = typename Vec2<V>::T;
   constexpr int NW = BT / 32 - 1;  // worker warps
-  __shared__ double wpart[kUnitGroup][NW];
+  __shared__ float wpart[kUnitGroup][NW];
+  __shared__ float sh_ab[2];       // beta, alpha
+  __shared__ int sh_ctl[3];        // stop flag, status, iterations
   *status_out = FCT_OK;
   *iters_out = 0;
   *gamma_out = gamma0;
-  if (!(gamma0 > 0.0)) {
+  if (!(gamma0 > 0.0) || !isfinite(gamma0)) {
     if (!isfinite(gamma0)) *status_out = FCT_ERR_NONFINITE;
     return true;
   }
@@ -524,28 +596,33 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   const int wk = static_cast<int>(threadIdx.x) - 32;  // worker index; warp 0 has wk < 0
   const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
   const int lane32 = threadIdx.x & 31;
-  double gamma = gamma0, best = gamma0;
+  const V rs = static_cast<V>(1.0 / sqrt(gamma0));   // squares are taken relative to gamma0
+  const float tol2 = static_cast<float>(tol * tol);
+  // thread 0's state (relative gamma)
+  float gam = 1.0f, best = 1.0f;
   int it = 0, best_it = 0;
   bool first = true;
-  // per-warp partial of the k-th unit of the current group -> shared
-  auto warp_part = [&](int kk, double v) {
+  auto relsq = [&](V v) {
+    const float t = static_cast<float>(v * rs);
+    return t * t;
+  };
+  auto warp_part = [&](int kk, float v) {
     v = warp_sum(v);
     if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
   };
-  // flush: unit partial = sum of its warps' partials, in warp order
-  auto flush = [&](double* part, int u0, int nk) {
+  auto flush = [&](float* part, int u0, int nk) {
     __syncthreads();
     if (threadIdx.x < nk) {
-      double v = 0.0;
+      float v = 0.0f;
 #pragma unroll
       for (int w2 = 0; w2 < NW; ++w2) v += wpart[threadIdx.x][w2];
       stcg(part + u0 + threadIdx.x * tm.G, v);
     }
     __syncthreads();
   };
+  int ctl = 0;
   for (;;) {
     // ================= phase A: q = A s + beta A p
-    double beta = 0.0;
     {
       auto gather_a = [&](int u, int k, V* as, V* ap, int* row, bool* lead) {
         row_gather_sp<V, V2, WT>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
@@ -556,55 +633,56 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       bool lead = false;
       if (wk >= 0) {
         if (u < nru) gather_a(u, 0, &as, &ap, &row, &lead);
-      } else if (!first) {
-        warp0_team_sum<BT>(P.part_c, ncc, red);
-      }
-      __syncthreads();
-      bool done = false;
-      if (!first) {
-        const double gnew = red[BT / 32];
-        ++it;
-        if (!isfinite(gnew)) {
-          *status_out = FCT_ERR_NONFINITE;
-          done = true;
-        } else {
-          beta = gnew / gamma;
-          gamma = gnew;
-          if (sqrt(gamma / gamma0) <= tol) {
-            done = true;
-          } else if (it >= max_iter) {
-            *status_out = FCT_ERR_NOCONV;
-            done = true;
-          } else if (stall > 0) {
-            if (gamma < best) {
-              best = gamma;
-              best_it = it;
-            } else if (it - best_it >= stall) {
-              done = true;
+      } else {
+        float gnew = 1.0f;
+        if (!first) gnew = warp0_team_sum_f(P.pc32, ncc);
+        if (threadIdx.x == 0) {
+          int c = 0;
+          float bt = 0.0f;
+          if (!first) {
+            ++it;
+            if (!isfinite(gnew)) {
+              c = FCT_ERR_NONFINITE + 16;
+            } else {
+              bt = gnew / gam;
+              gam = gnew;
+              if (gam <= tol2) c = 1;
+              else if (it >= max_iter) c = FCT_ERR_NOCONV + 16;
+              else if (stall > 0) {
+                if (gam < best) {
+                  best = gam;
+                  best_it = it;
+                } else if (it - best_it >= stall) {
+                  c = 1;
+                }
+              }
             }
           }
+          sh_ab[0] = bt;
+          sh_ctl[0] = c;
         }
       }
       __syncthreads();
-      if (done) break;
+      ctl = sh_ctl[0];
+      if (ctl != 0) break;
+      const V beta = static_cast<V>(sh_ab[0]);
       int k = 0, kg = 0, u0 = u;
       for (; u < nru; u += tm.G, ++k) {
         if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
-        double part = 0.0;
+        float part = 0.0f;
         if (wk >= 0 && lead) {
-          const V qv = first ? as : fma(static_cast<V>(beta), ap, as);
+          const V qv = first ? as : fma(beta, ap, as);
           stcg(q + row, qv);
-          part = static_cast<double>(qv) * static_cast<double>(qv);
+          part = relsq(qv);
         }
         warp_part(kg, part);
-        if (++kg == kUnitGroup) {
-          flush(P.part_r, u0, kg);
+        if (++kg == kUnitGroup && u + tm.G < nru) {
+          flush(P.pr32, u0, kg);
           kg = 0;
           u0 = u + tm.G;
         }
       }
-      if (kg > 0) flush(P.part_r, u0, kg);
-      if (!team_sync(tm)) return false;
+      if (!phase_end<NW>(tm, wpart, P.pr32, u0, kg)) return false;
     }
     // ================= phase B: t = A^T q; {s, p} and x updated by the owner
     {
@@ -628,48 +706,61 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           t = coef_gather<V, WT>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
         }
       } else {
-        warp0_team_sum<BT>(P.part_r, nru, red);
+        const float dl = warp0_team_sum_f(P.pr32, nru);
+        if (threadIdx.x == 0) {
+          int cc = 0;
+          float al = 0.0f;
+          if (!isfinite(dl)) cc = FCT_ERR_NONFINITE + 16;
+          else if (!(dl > 0.0f)) cc = 1;  // q = 0: s is already zero to working precision
+          else al = gam / dl;
+          sh_ab[1] = al;
+          sh_ctl[0] = cc;
+        }
       }
       __syncthreads();
-      const double delta = red[BT / 32];
-      __syncthreads();
-      if (!isfinite(delta)) {
-        *status_out = FCT_ERR_NONFINITE;
-        break;
-      }
-      if (!(delta > 0.0)) break;  // q = 0: s is already zero to working precision
-      const double alpha = gamma / delta;
+      ctl = sh_ctl[0];
+      if (ctl != 0) break;
+      const V alpha = static_cast<V>(sh_ab[1]);
+      const V beta = static_cast<V>(sh_ab[0]);
       int k = 0, kg = 0, c0 = c;
       for (; c < ncc; c += tm.G, ++k) {
         if (k > 0 && wk >= 0) {
           own_load(c, &o, &xo);
           t = coef_gather<V, WT>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
         }
-        double part = 0.0;
+        float part = 0.0f;
         if (wk >= 0 && lead) {
-          const V pn = first ? o.x : fma(static_cast<V>(beta), o.y, o.x);
-          const V sn = fma(static_cast<V>(-alpha), t, o.x);
+          const V pn = first ? o.x : fma(beta, o.y, o.x);
+          const V sn = fma(-alpha, t, o.x);
           V2 nv;
           nv.x = sn;
           nv.y = pn;
           stcg(sp + m, nv);
           stcg(x + m, static_cast<XT>(fma(static_cast<XT>(alpha), static_cast<XT>(pn), xo)));
-          part = static_cast<double>(sn) * static_cast<double>(sn);
+          part = relsq(sn);
         }
         warp_part(kg, part);
-        if (++kg == kUnitGroup) {
-          flush(P.part_c, c0, kg);
+        if (++kg == kUnitGroup && c + tm.G < ncc) {
+          flush(P.pc32, c0, kg);
           kg = 0;
           c0 = c + tm.G;
         }
       }
-      if (kg > 0) flush(P.part_c, c0, kg);
-      if (!team_sync(tm)) return false;
+      if (!phase_end<NW>(tm, wpart, P.pc32, c0, kg)) return false;
     }
     first = false;
   }
-  *iters_out = it;
-  *gamma_out = gamma;
+  // broadcast thread 0's final state
+  if (threadIdx.x == 0) {
+    sh_ctl[1] = ctl >= 16 ? ctl - 16 : FCT_OK;
+    sh_ctl[2] = it;
+    sh_ab[0] = gam;
+  }
+  __syncthreads();
+  *status_out = sh_ctl[1];
+  *iters_out = sh_ctl[2];
+  *gamma_out = static_cast<double>(sh_ab[0]) * gamma0;
+  __syncthreads();
   return true;
 }
 
@@ -1169,9 +1260,26 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.coefs_per_chunk = workers / L;
   hp.n_coef_chunks = static_cast<int32_t>((N + hp.coefs_per_chunk - 1) / hp.coefs_per_chunk);
   hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
-  device_row_order(&H);
+  // Entries per gather lane: the smallest of 2, 4, 8 whose row units fit in
+  // one wave of co-resident blocks (a block with two units while others have
+  // one makes everybody wait at the next barrier).
+  int epl = 8;
+  {
+    int per_sm = 0, nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(BT), BT, 0) == cudaSuccess) {
+      const int64_t wave = static_cast<int64_t>(per_sm) * nsm;
+      for (int e : {2, 4, 8})
+        if (count_row_units(H, workers, e) <= wave) {
+          epl = e;
+          break;
+        }
+    }
+  }
+  device_row_order(&H, epl);
   std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
-  row_units(H, workers, &ru_first, &ru_lanes);
+  row_units(H, workers, epl, &ru_first, &ru_lanes);
   final_pass_rows(H, &rowbase, &rowk);
   hp.n_row_units = static_cast<int32_t>(ru_lanes.size());
   hp.n_mats = static_cast<int32_t>(H.dct_mats.size());
@@ -1220,6 +1328,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&hp.sp, sizeof(double2) * N);
   add(&hp.part_r, sizeof(double) * hp.n_row_units);
   add(&hp.part_c, sizeof(double) * hp.n_coef_chunks);
+  add(&hp.pr32, sizeof(float) * hp.n_row_units);
+  add(&hp.pc32, sizeof(float) * hp.n_coef_chunks);
   add(&hp.q32, sizeof(float) * H.R);
   add(&hp.sp32, sizeof(float2) * N);
   add(&hp.dx32, sizeof(float) * N);
@@ -1530,7 +1640,7 @@ std::mutex g_noalloc_mu;
 
 // Layout of the workspace inside the array (256-byte aligned pieces).
 struct NoallocLayout {
-  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, q32, sp32, dx32, total;
+  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, pr32, pc32, q32, sp32, dx32, total;
 };
 
 NoallocLayout noalloc_layout(const fct_plan P) {
@@ -1554,6 +1664,8 @@ NoallocLayout noalloc_layout(const fct_plan P) {
   L.sp = take(sizeof(double2) * N);
   L.part_r = take(sizeof(double) * P->hp.n_row_units);
   L.part_c = take(sizeof(double) * P->hp.n_coef_chunks);
+  L.pr32 = take(sizeof(float) * P->hp.n_row_units);
+  L.pc32 = take(sizeof(float) * P->hp.n_coef_chunks);
   L.q32 = take(sizeof(float) * R);
   L.sp32 = take(sizeof(float2) * N);
   L.dx32 = take(sizeof(float) * N);
@@ -1600,6 +1712,8 @@ extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, dou
   hp.sp = reinterpret_cast<double2*>(b + L.sp);
   hp.part_r = reinterpret_cast<double*>(b + L.part_r);
   hp.part_c = reinterpret_cast<double*>(b + L.part_c);
+  hp.pr32 = reinterpret_cast<float*>(b + L.pr32);
+  hp.pc32 = reinterpret_cast<float*>(b + L.pc32);
   hp.q32 = reinterpret_cast<float*>(b + L.q32);
   hp.sp32 = reinterpret_cast<float2*>(b + L.sp32);
   hp.dx32 = reinterpret_cast<float*>(b + L.dx32);

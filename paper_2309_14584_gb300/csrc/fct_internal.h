@@ -16,7 +16,6 @@ namespace fct {
 constexpr int kMaxD = 255;
 constexpr int kDctChunk = 1024;        // elements of one grid per DCT work unit
 constexpr int kMaxTeams = 1024;        // teams per launch (batched execute)
-constexpr int kEntriesPerLane = 2;     // target CSR entries per thread in the A p gather
 constexpr int kMaxAxis = 4096;         // longest grid axis (points) the direct DCT-I accepts
 
 // One DCT-I work unit: a contiguous element range of one grid tensor in one
@@ -78,8 +77,10 @@ struct DevPlan {
   double* rres;              // [R] FP64 residual b - A x (mixed path sweeps)
   double* q;                 // [R]
   double2* sp;               // [N] {s, p} interleaved: one 16-byte gather per entry
-  double* part_r;            // [n_row_units]
+  double* part_r;            // [n_row_units]    FP64 partials (set-up and refinement phases)
   double* part_c;            // [n_coef_chunks]
+  float* pr32;               // [n_row_units]    FP32 partials of the CG loop (relative |q|^2)
+  float* pc32;               // [n_coef_chunks]  (relative |s|^2)
   // FP32 workspace of the mixed path
   float* q32;                // [R]
   float2* sp32;              // [N] {s, p} of the inner FP32 solve
@@ -151,16 +152,20 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
                              const int32_t* sizes, const double* nodes, bool with_dct,
                              HostTables* out, std::string* err);
 
-// Renumber the rows of H for the device: stable sort by descending gather
-// lane count (see row_units), so that rows with equal lane counts are
-// contiguous and keep their ascending-bin order.
-// Rewrites rowptr, col, wcsr, rowsrc, rowgrid and crow in place.
-void device_row_order(HostTables* H);
+// Gather lanes of a row with len entries: min(32, pow2 >= ceil(len / epl)),
+// epl = target entries per lane.
+int lanes_for(int32_t len, int epl);
 
-// A p gather units for `workers` threads per block: rows get
-// min(32, pow2 >= ceil(len / kEntriesPerLane)) lanes; a unit holds
+// Renumber the rows of H for the device: stable sort by descending gather
+// lane count, so that rows with equal lane counts are contiguous and keep
+// their ascending-bin order.  Rewrites rowptr, col, wcsr, rowsrc, rowgrid and
+// crow in place.
+void device_row_order(HostTables* H, int epl);
+
+// A p gather units for `workers` threads per block: a unit holds
 // workers / lanes consecutive rows of equal lane count.
-void row_units(const HostTables& H, int workers, std::vector<int32_t>* first, std::vector<int32_t>* lanes);
+int64_t count_row_units(const HostTables& H, int workers, int epl);
+void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* first, std::vector<int32_t>* lanes);
 
 // Per-row inputs of the fused last DCT pass (after device_row_order).
 void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::vector<int32_t>* rowk);

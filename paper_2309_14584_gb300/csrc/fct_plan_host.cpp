@@ -268,9 +268,7 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
   return FCT_OK;
 }
 
-static int lanes_for(int32_t len);
-
-void device_row_order(HostTables* Hp) {
+void device_row_order(HostTables* Hp, int epl) {
   HostTables& H = *Hp;
   const int64_t R = H.R;
   std::vector<int32_t> order(R);
@@ -278,7 +276,7 @@ void device_row_order(HostTables* Hp) {
   // stable sort by gather lane class only: rows keep their bin order within a
   // class, which keeps neighbouring coefficients' rows close together
   std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return lanes_for(H.rowptr[a + 1] - H.rowptr[a]) > lanes_for(H.rowptr[b + 1] - H.rowptr[b]);
+    return lanes_for(H.rowptr[a + 1] - H.rowptr[a], epl) > lanes_for(H.rowptr[b + 1] - H.rowptr[b], epl);
   });
   std::vector<int32_t> inv(R), rowptr(R + 1), col(H.col.size()), rowsrc(R), rowgrid(R);
   std::vector<double> wcsr(H.wcsr.size());
@@ -301,22 +299,37 @@ void device_row_order(HostTables* Hp) {
   H.rowgrid.swap(rowgrid);
 }
 
-static int lanes_for(int32_t len) {
+int lanes_for(int32_t len, int epl) {
   int lanes = 1;
-  while (lanes < 32 && lanes * kEntriesPerLane < len) lanes <<= 1;
+  while (lanes < 32 && lanes * epl < len) lanes <<= 1;
   return lanes;
 }
 
-void row_units(const HostTables& H, int workers, std::vector<int32_t>* first, std::vector<int32_t>* lanes) {
+int64_t count_row_units(const HostTables& H, int workers, int epl) {
+  // rows sorted or not, the unit count only depends on the rows per lane class
+  int64_t per_class[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t r = 0; r < H.R; ++r) {
+    const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r], epl);
+    per_class[__builtin_ctz(static_cast<unsigned>(lc))]++;
+  }
+  int64_t units = 0;
+  for (int c = 0; c < 6; ++c) {
+    const int64_t per = workers >> c;
+    units += (per_class[c] + per - 1) / per;
+  }
+  return units;
+}
+
+void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* first, std::vector<int32_t>* lanes) {
   first->clear();
   lanes->clear();
   int64_t r = 0;
   while (r < H.R) {
-    const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r]);
+    const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r], epl);
     const int per = workers / lc;
     int64_t e = r;
-    // rows are sorted by descending length, so equal lane counts are contiguous
-    while (e < H.R && e - r < per && lanes_for(H.rowptr[e + 1] - H.rowptr[e]) == lc) ++e;
+    // rows are sorted by lane class, so equal lane counts are contiguous
+    while (e < H.R && e - r < per && lanes_for(H.rowptr[e + 1] - H.rowptr[e], epl) == lc) ++e;
     first->push_back(static_cast<int32_t>(r));
     lanes->push_back(lc);
     r = e;

@@ -222,3 +222,20 @@ def test_nonfinite_samples_reported():
     plan.sample(w.family, w.params, s)
     assert plan.execute(s, c)["status"] == 0
     plan.close()
+
+
+@pytest.mark.slow
+def test_d10_rational_full_size_fp64_and_mixed_match_oracle():
+    """D=10, total degree 8 (N=43758), 30 grids, rational target, at full
+    size: the FP64 path within 1e-11 and the mixed path within 1e-10 of the
+    oracle's FP64 CGLS solution (tolerance 1e-15 on |A^T r| / |A^T b|)."""
+    w = W.config_d10_rational()
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    system = O.AliasSystem(w.support, w.sizes, w.nodes)
+    ref, it, relres = O.cgls(system.A, system.rhs(f), tol=1e-15)
+    got64, s_gpu, rep64 = gpu_run(w, samples_np=f, precision=F.FCT_FP64, tol=1e-13)
+    assert rep64["status"] == 0
+    assert rel(got64, ref) <= TOL_FP64, (rel(got64, ref), rep64)
+    gotmx, _, repmx = gpu_run(w, samples_np=f, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
+    assert repmx["status"] == 0
+    assert rel(gotmx, ref) <= TOL_MIXED, (rel(gotmx, ref), repmx)
