@@ -63,14 +63,18 @@ enum {
   FCT_FAMILY_POLY = 0,          /* sum_m c_m T_m(x); params = c[N] (support order)        */
   FCT_FAMILY_GAUSSCOS = 1,      /* exp(-sum a_i x_i^2) cos(sum b_i x_i); params = a[D],b[D] */
   FCT_FAMILY_RATIONAL = 2,      /* 1/(1 + sum c_i x_i^2); params = c[D]                    */
-  FCT_FAMILY_POLY_GAUSSCOS = 3  /* gausscos + poly; params = a[D], b[D], c[N]              */
+  FCT_FAMILY_POLY_GAUSSCOS = 3, /* gausscos + poly; params = a[D], b[D], c[N]              */
+  FCT_SAMPLE_FOLDED = 0x100     /* flag OR-ed into a polynomial family: evaluate the
+                                   polynomial through its bins (see fct_sample)          */
 };
 
 typedef struct fct_plan_s* fct_plan;
 
 typedef struct {
-  int precision;      /* FCT_FP64: FP64 CGLS.  FCT_MIXED: FP32 inner CGLS with FP64
-                         residual, FP64 reductions and FP64 refinement sweeps.          */
+  int precision;      /* FCT_FP64: FP64 CG on the normal equations.  FCT_MIXED: FP32
+                         inner solves between FP64 residual sweeps; if a sweep gains
+                         less than one digit (ill-conditioned L-grid) or max_refine
+                         sweeps pass, the solve continues in FP64 from the current x. */
   double tol;         /* stop when ||A^T r|| <= tol * ||A^T b|| (FP64 measure)           */
   int max_iter;       /* cap on CGLS iterations (FP64) / inner iterations per sweep     */
   double inner_tol;   /* FCT_MIXED: relative tolerance of each inner FP32 solve         */
@@ -103,7 +107,7 @@ typedef struct {
   int64_t device_bytes;     /* tables + workspace held on the device               */
 } fct_plan_info;
 
-/* Fill *opt with defaults: FP64, tol 1e-13, max_iter 20000, inner_tol 1e-6,
+/* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,
  * max_refine 6, automatic launch shape, 4 s wait bound. */
 void fct_default_options(fct_options* opt);
 
@@ -139,6 +143,11 @@ fct_status fct_grid_offsets(fct_plan plan, int64_t* offsets);
  * Algorithm 3).  params host double[nparams] laid out per FCT_FAMILY_*;
  * samples device double[M].  Asynchronous on stream (params are staged
  * through plan-owned device memory before returning).
+ * Polynomial families are evaluated term by term (M*N*D work) unless M*N
+ * exceeds 4e10 or FCT_SAMPLE_FOLDED is set: then the coefficients are folded
+ * into each grid's bins (the alias map) and the grid interpolant is evaluated
+ * at the nodes, axis by axis (O(K N + M sum n) work).  The folded path uses
+ * the plan's workspace: it must not overlap an execute on the same plan.
  */
 fct_status fct_sample(fct_plan plan, int family, const double* params, int64_t nparams,
                       double* samples, void* stream);

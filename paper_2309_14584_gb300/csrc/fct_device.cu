@@ -872,6 +872,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         double part = 0.0;
         if (lead) {
           stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));
+          stcg(P.sp + m, make_double2(t, 0.0));  // for an FP64 continuation
           stcg(P.dx32 + m, 0.0f);
           part = t * t;
         }
@@ -879,15 +880,27 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         if (threadIdx.x == 0) stcg(P.part_c + c, part);
       }
       if (!team_sync(tm)) return false;
+      const double g_prev = g64;
       g64 = team_sum<BT>(P.part_c, ncc, red);
       gfinal = g64;
       if (!isfinite(g64)) {
         status = FCT_ERR_NONFINITE;
         break;
       }
-      if (!(g64 > 0.0) || sqrt(g64 / gamma0) <= J.tol) break;
-      if (k + 1 >= J.max_refine) {
-        status = FCT_ERR_NOCONV;
+      if (!(g64 > 0.0) || g64 <= J.tol * J.tol * gamma0) break;
+      if (k + 1 >= J.max_refine || g64 > 1e-2 * g_prev) {
+        // FP32 inner solves no longer gain a digit per sweep (an ill-conditioned
+        // L-grid): finish in FP64 from the current x, starting from this sweep's
+        // exact normal residual g (in sp).
+        int it64 = 0, st64 = FCT_OK;
+        double g_out = g64;
+        const double tol_eff = J.tol * sqrt(gamma0 / g64);
+        if (!cg_normal<BT, double, double, double>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, x, g64, tol_eff, J.max_iter,
+                                                   0, &it64, &g_out, &st64, red))
+          return false;
+        iters += it64;
+        gfinal = g_out;
+        status = st64;
         break;
       }
     }
@@ -1031,6 +1044,42 @@ __global__ void sample_kernel(const SampleArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Polynomial samples through the bins (fast sampler): p restricted to grid l
+// is the grid interpolant whose coefficient at bin k is (A^(l) c)_k, so
+//   y0 = A c scattered to the full bin tensors, then T_k(x_j) evaluation
+// along every active axis gives p at the grid points.  Cost O(KN + M sum n)
+// instead of O(M N D) for term-by-term evaluation.
+// ---------------------------------------------------------------------------
+__global__ void fold_scatter_kernel(const DevPlan* __restrict__ Pp, const double* __restrict__ c) {
+  const DevPlan& P = *Pp;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= P.R) return;
+  double acc = 0.0;
+  const int j1 = P.rowptr[row + 1];
+  for (int j = P.rowptr[row]; j < j1; ++j) acc = fma(P.wcsr[j], c[P.col[j]], acc);
+  const GridFinal g = P.gfinal[P.rowgrid[row]];
+  P.y0[P.rowbase[row] + static_cast<int64_t>(P.rowk[row]) * g.stride] = acc;
+}
+
+__global__ void eval_pass_kernel(const DevPlan* __restrict__ Pp, const DctChunk* __restrict__ chunks, int c0,
+                                 const double* __restrict__ mats, double* samples, int add) {
+  const DevPlan& P = *Pp;
+  const DctChunk ch = chunks[c0 + blockIdx.x];
+  const double* in = (ch.in_sel == 1 ? P.y0 : P.y1) + ch.base;
+  double* out = (ch.out_sel == 3 ? samples : (ch.out_sel == 1 ? P.y0 : P.y1)) + ch.base;
+  const double* E = mats + ch.mat;
+  for (int e = ch.start + threadIdx.x; e < ch.start + ch.count; e += blockDim.x) {
+    const int j = (e / ch.stride) % ch.n;  // output node index on this axis
+    const int base = e - j * ch.stride;
+    const double* Ej = E + j * ch.n;
+    double acc = 0.0;
+    for (int k = 0; k < ch.n; ++k) acc = fma(Ej[k], in[base + k * ch.stride], acc);
+    if (ch.out_sel == 3 && add) acc += out[e];
+    out[e] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 struct fct_plan_s {
@@ -1057,6 +1106,8 @@ struct fct_plan_s {
   double* d_node_pos = nullptr;
   uint16_t* d_support = nullptr;
   double* d_ttab = nullptr;
+  DctChunk* d_ichunks = nullptr;   // evaluation passes of the fast sampler
+  double* d_emats = nullptr;
   double* d_params = nullptr;
   int64_t params_cap = 0;
   // host-buffer execute staging
@@ -1339,6 +1390,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&P->d_node_pos, sizeof(double) * nnodes);
   add(&P->d_support, sizeof(uint16_t) * N * D);
   add(&P->d_ttab, sizeof(double) * nnodes * (P->dmax + 1));
+  add(&P->d_ichunks, sizeof(DctChunk) * H.idct_chunks.size());
+  add(&P->d_emats, sizeof(double) * H.eval_mats.size());
   size_t total = 0;
   for (auto& pc : pieces) total += align256(std::max<size_t>(pc.bytes, 1));
   cudaError_t e = cudaMalloc(&P->dmem, total);
@@ -1407,6 +1460,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(P->d_node_off, H.node_off.data(), sizeof(int32_t) * K * D));
   chk(up(P->d_node_pos, H.node_pos.data(), sizeof(double) * nnodes));
   chk(up(P->d_support, support, sizeof(uint16_t) * N * D));
+  chk(up(P->d_ichunks, H.idct_chunks.data(), sizeof(DctChunk) * H.idct_chunks.size()));
+  chk(up(P->d_emats, H.eval_mats.data(), sizeof(double) * H.eval_mats.size()));
   s = FCT_OK;
   if (ue == cudaSuccess) s = choose_shape(P);
   if (ue == cudaSuccess && s == FCT_OK) chk(up(P->dp, &hp, sizeof(DevPlan)));
@@ -1456,6 +1511,8 @@ fct_status fct_grid_offsets(fct_plan P, int64_t* offsets) {
 fct_status fct_sample(fct_plan P, int family, const double* params, int64_t nparams, double* samples,
                       void* stream) {
   if (!P || !params || !samples) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  const bool force_folded = (family & FCT_SAMPLE_FOLDED) != 0;
+  family &= ~FCT_SAMPLE_FOLDED;
   int64_t need = 0;
   switch (family) {
     case FCT_FAMILY_POLY: need = P->N; break;
@@ -1465,6 +1522,10 @@ fct_status fct_sample(fct_plan P, int family, const double* params, int64_t npar
     default: return fail(FCT_ERR_INVALID_ARG, "unknown family");
   }
   if (nparams != need) return fail(FCT_ERR_INVALID_ARG, "params length does not match the family");
+  const bool poly = family == FCT_FAMILY_POLY || family == FCT_FAMILY_POLY_GAUSSCOS;
+  if (force_folded && !poly) return fail(FCT_ERR_INVALID_ARG, "FCT_SAMPLE_FOLDED applies to polynomial families");
+  // term-by-term evaluation costs M*N*D; above this the folded path is used
+  const bool folded = poly && (force_folded || static_cast<double>(P->M) * static_cast<double>(P->N) > 4e10);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (nparams > P->params_cap) {
     if (P->d_params) {
@@ -1490,11 +1551,25 @@ fct_status fct_sample(fct_plan P, int family, const double* params, int64_t npar
   a.K = P->K;
   a.D = P->D;
   a.N = static_cast<int>(P->N);
-  a.family = family;
+  a.family = folded ? (family == FCT_FAMILY_POLY_GAUSSCOS ? FCT_FAMILY_GAUSSCOS : -1) : family;
   a.dmax = P->dmax;
   const int bt = 128;
-  sample_kernel<<<static_cast<unsigned>((P->M + bt - 1) / bt), bt, 0, st>>>(a);
-  FCT_CUDA(cudaGetLastError());
+  if (a.family >= 0) {
+    sample_kernel<<<static_cast<unsigned>((P->M + bt - 1) / bt), bt, 0, st>>>(a);
+    FCT_CUDA(cudaGetLastError());
+  }
+  if (folded) {
+    const double* c = P->d_params + (family == FCT_FAMILY_POLY_GAUSSCOS ? 2 * P->D : 0);
+    FCT_CUDA(cudaMemsetAsync(P->hp.y0, 0, sizeof(double) * P->M, st));
+    fold_scatter_kernel<<<static_cast<unsigned>((P->R + 255) / 256), 256, 0, st>>>(P->dp, c);
+    FCT_CUDA(cudaGetLastError());
+    const int add = family == FCT_FAMILY_POLY_GAUSSCOS ? 1 : 0;
+    for (int p = 0; p < P->H.nipass; ++p) {
+      const int c0 = P->H.ipass_chunk_off[p], c1 = P->H.ipass_chunk_off[p + 1];
+      if (c1 > c0) eval_pass_kernel<<<c1 - c0, 256, 0, st>>>(P->dp, P->d_ichunks, c0, P->d_emats, samples, add);
+      FCT_CUDA(cudaGetLastError());
+    }
+  }
   return FCT_OK;
 }
 
@@ -1576,8 +1651,18 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
     P0->djobs_cap = B;
   }
   fct_report* dreps = reinterpret_cast<fct_report*>(P0->djobs + P0->djobs_cap);
+  // Queue order: largest transforms first (longest-processing-time-first keeps
+  // the tail short); each job still writes its own caller's report slot.
+  std::vector<int> order(B);
+  for (int i = 0; i < B; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return plans[a]->hp.K * static_cast<int64_t>(plans[a]->N) > plans[b]->hp.K * static_cast<int64_t>(plans[b]->N);
+  });
   std::vector<SolveJob> jobs(B);
-  for (int i = 0; i < B; ++i) jobs[i] = make_job(plans[i], samples[i], coeffs[i], dreps + i);
+  for (int q = 0; q < B; ++q) {
+    const int i = order[q];
+    jobs[q] = make_job(plans[i], samples[i], coeffs[i], dreps + i);
+  }
   FCT_CUDA(cudaMemcpyAsync(P0->djobs, jobs.data(), sizeof(SolveJob) * B, cudaMemcpyHostToDevice, st));
   FCT_CUDA(cudaStreamSynchronize(st));
   int G = team_blocks;

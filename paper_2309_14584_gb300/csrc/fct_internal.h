@@ -26,7 +26,7 @@ struct DctChunk {
   int32_t start, count;    // element range within the grid tensor
   int32_t n, stride;       // axis length (1 = identity copy) and its stride
   int32_t mat;             // offset of the n x n matrix in dct_mats
-  int8_t in_sel, out_sel;  // 0 = caller samples, 1 = y0, 2 = y1
+  int8_t in_sel, out_sel;  // 0 = caller samples, 1 = y0, 2 = y1, 3 = caller samples (output)
   int16_t pad;
 };
 static_assert(sizeof(DctChunk) == 32, "DctChunk layout");
@@ -141,6 +141,13 @@ struct HostTables {
   std::vector<DctChunk> dct_chunks;
   std::vector<double> dct_mats;
   std::vector<GridFinal> gfinal;       // [K]
+  // inverse transform (sampler of polynomials through the bins): evaluation
+  // passes over every active axis, y0/y1 ping-pong, the last into the caller's
+  // samples (out_sel 3)
+  int nipass = 0;
+  std::vector<int32_t> ipass_chunk_off;  // [nipass+1]
+  std::vector<DctChunk> idct_chunks;
+  std::vector<double> eval_mats;         // E[j][k] = T_k(x_j) per distinct axis length
   // sampler geometry: node positions of every grid axis
   std::vector<int32_t> node_off;       // [K*D] offset of grid l axis i in nodes
   std::vector<double> node_pos;

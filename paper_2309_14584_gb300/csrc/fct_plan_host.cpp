@@ -236,6 +236,61 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
     }
     H.gfinal[l] = g;
   }
+  // Evaluation passes of the sampler: every active axis, E[j][k] = T_k(x_j),
+  // pass p reads y0 (p = 0) or the previous output and the last pass writes
+  // the caller's samples; a grid without active axes gets one copy pass.
+  {
+    std::vector<int32_t> emat_of;
+    auto eval_for = [&](int32_t n) -> int32_t {
+      if (static_cast<int32_t>(emat_of.size()) <= n) emat_of.resize(n + 1, -1);
+      if (emat_of[n] >= 0) return emat_of[n];
+      const int32_t off = static_cast<int32_t>(H.eval_mats.size());
+      if (n == 1) {
+        H.eval_mats.push_back(1.0);
+      } else {
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k)
+            H.eval_mats.push_back(cos_pi_ratio((static_cast<int64_t>(j) * k) % (2 * (n - 1)), n - 1));
+      }
+      emat_of[n] = off;
+      return off;
+    };
+    int nip = 0;
+    for (int l = 0; l < K; ++l) nip = std::max<int>(nip, std::max<size_t>(1, active[l].size()));
+    H.nipass = nip;
+    H.ipass_chunk_off.assign(1, 0);
+    for (int p = 0; p < nip; ++p) {
+      for (int l = 0; l < K; ++l) {
+        const int A = std::max<int>(1, static_cast<int>(active[l].size()));
+        if (p >= A) continue;
+        int32_t n = 1;
+        int64_t st = 1;
+        if (!active[l].empty()) {
+          const int axis = active[l][p];
+          n = sizes[l * D + axis];
+          for (int i = axis + 1; i < D; ++i) st *= sizes[l * D + i];
+        }
+        const int32_t mat = eval_for(n);
+        const int8_t in_sel = p == 0 ? 1 : static_cast<int8_t>(((p - 1) & 1) ? 1 : 2);
+        const int8_t out_sel = p == A - 1 ? 3 : static_cast<int8_t>((p & 1) ? 1 : 2);
+        const int64_t T = H.offsets[l + 1] - H.offsets[l];
+        for (int64_t e0 = 0; e0 < T; e0 += kDctChunk) {
+          DctChunk c{};
+          c.base = H.offsets[l];
+          c.start = static_cast<int32_t>(e0);
+          c.count = static_cast<int32_t>(std::min<int64_t>(kDctChunk, T - e0));
+          c.n = n;
+          c.stride = static_cast<int32_t>(st);
+          c.mat = mat;
+          c.in_sel = in_sel;
+          c.out_sel = out_sel;
+          H.idct_chunks.push_back(c);
+        }
+      }
+      H.ipass_chunk_off.push_back(static_cast<int32_t>(H.idct_chunks.size()));
+    }
+  }
+
   H.npass = npass;
   H.pass_chunk_off.assign(1, 0);
   for (int p = 0; p < npass; ++p) {
@@ -376,7 +431,7 @@ void fct_default_options(fct_options* opt) {
   std::memset(opt, 0, sizeof(*opt));
   opt->precision = FCT_FP64;
   opt->tol = 1e-13;
-  opt->max_iter = 20000;
+  opt->max_iter = 50000;
   opt->inner_tol = 1e-6;
   opt->max_refine = 6;
   opt->block_threads = 0;

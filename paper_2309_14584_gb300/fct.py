@@ -30,6 +30,7 @@ FCT_FAMILY_POLY = 0
 FCT_FAMILY_GAUSSCOS = 1
 FCT_FAMILY_RATIONAL = 2
 FCT_FAMILY_POLY_GAUSSCOS = 3
+FCT_SAMPLE_FOLDED = 0x100
 
 
 class fct_options(ctypes.Structure):

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_default_options_and_status_strings(lib):
     o = F.fct_default_options()
-    assert o.precision == F.FCT_FP64 and o.tol == 1e-13 and o.max_iter == 20000
+    assert o.precision == F.FCT_FP64 and o.tol == 1e-13 and o.max_iter == 50000
     assert F.fct.status_string(0) == "FCT_OK"
     assert F.fct.status_string(4) == "FCT_ERR_TIMEOUT"
 

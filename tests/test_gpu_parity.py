@@ -239,3 +239,63 @@ def test_d10_rational_full_size_fp64_and_mixed_match_oracle():
     gotmx, _, repmx = gpu_run(w, samples_np=f, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
     assert repmx["status"] == 0
     assert rel(gotmx, ref) <= TOL_MIXED, (rel(gotmx, ref), repmx)
+
+
+FOLDED_CASES = [
+    ("D2_poly", 51, 2, 16, 4, 9, 33, W.FAMILY_POLY),
+    ("D4_poly", 52, 4, 6, 12, 1, 7, W.FAMILY_POLY),
+    ("D4_polygc", 53, 4, 6, 12, 1, 7, W.FAMILY_POLY_GAUSSCOS),
+    ("D6_poly", 54, 6, 5, 18, 1, 6, W.FAMILY_POLY),
+]
+
+
+@pytest.mark.parametrize("case", FOLDED_CASES, ids=[c[0] for c in FOLDED_CASES])
+def test_folded_polynomial_sampler_matches_term_by_term_and_oracle(case):
+    """The fast sampler (coefficients folded into bins, grid interpolant
+    evaluated at the nodes) equals term-by-term evaluation on the device and
+    the oracle's brute-force samples."""
+    w = _small(case)
+    plan = F.Plan(w.support, w.sizes, w.nodes)
+    s_term = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    s_fold = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    plan.sample(w.family, w.params, s_term)
+    plan.sample(w.family | F.fct.FCT_SAMPLE_FOLDED, w.params, s_fold)
+    torch.cuda.synchronize()
+    a, b = s_term.cpu().numpy(), s_fold.cpu().numpy()
+    scale = max(1.0, np.max(np.abs(a)))
+    assert np.max(np.abs(a - b)) <= 1e-12 * scale
+    ref = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    assert np.max(np.abs(b - ref)) <= 1e-12 * scale
+    plan.close()
+
+
+@pytest.mark.slow
+def test_batch_of_512_mixed_transforms_equals_alone_and_oracle():
+    """The 512-transform batch (D in 3..8, degree 6..14, polynomial plus
+    Gaussian-cosine targets, mixed precision) in one persistent launch: every
+    result is bit-identical to the same transform solved alone, all converge,
+    and the smallest transforms match the oracle within 1e-10."""
+    ws = W.config_batch()
+    plans, samples, outs = [], [], []
+    for w in ws:
+        p = F.Plan(w.support, w.sizes, w.nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
+        s = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(w.family, w.params, s)
+        plans.append(p)
+        samples.append(s)
+        outs.append(torch.full((p.N,), float("nan"), dtype=torch.float64, device="cuda"))
+    reps = F.fct_execute_batch([p.handle for p in plans], samples, outs)
+    assert all(r["status"] == 0 for r in reps), [r for r in reps if r["status"] != 0][:3]
+    alone = torch.empty(max(p.N for p in plans), dtype=torch.float64, device="cuda")
+    for p, s, o in zip(plans, samples, outs):
+        a = alone[:p.N]
+        assert p.execute(s, a)["status"] == 0
+        assert torch.equal(a, o)
+    small = sorted(range(len(ws)), key=lambda i: ws[i].N)[:4]
+    for i in small:
+        w = ws[i]
+        f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+        ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+        assert rel(outs[i].cpu().numpy(), ref) <= TOL_MIXED, (w.name, rel(outs[i].cpu().numpy(), ref))
+    for p in plans:
+        p.close()
