@@ -177,21 +177,44 @@ class ClockSampler:
 # roofline bookkeeping
 # ---------------------------------------------------------------------------
 def algorithmic_bytes(info, rep, precision):
-    """Bytes the method must move per launch (one transform), as stated in the
-    design notes: DCT reads the samples and writes b; every CGLS iteration
-    streams the alias tables once in each orientation (col/crow int32 and the
-    entries in both orders) and touches each vector once."""
+    """Bytes the method must move per launch (one transform).
+
+    DCT: read the M samples once, write the R values of b.
+    One CG iteration on the normal equations (each table entry and each vector
+    element counted once): the alias tables in both orientations (column and
+    row indices, 4 bytes each, plus the entry value in the working precision),
+    {s, p} and x read and written by their owners, q written and read.
+        K N (8 + 2 w) + v (6 N + 2 R) + 2 v_x N
+    with w = v = v_x = 8 (FP64) or 4 (FP32 inner solve).  A mixed-path sweep
+    (x += c d, r = b - A x, g = A^T r, all FP64) adds
+        2 K N (4 + 8) + 8 (4 N + 3 R)."""
     N, R, K, M = info["N"], info["R"], info["K"], info["M"]
     dct = 8 * M + 8 * R
-    def it_bytes(vb, wb):
-        tables = K * N * (4 + 4 + 2 * wb) + 4 * R
-        vectors = vb * (7 * N + 4 * R)     # A: s, p_old, p_new, q ; B: r_old, q, s, p_new, x (rw), r_new
-        return tables + vectors
+
+    def it_bytes(w):
+        return K * N * (8 + 2 * w) + w * (6 * N + 2 * R) + 2 * w * N
+
     if precision == "fp64":
-        return dct + rep["iterations"] * it_bytes(8, 8)
-    refine = rep["refinements"] + 1
-    per_ref = 2 * (K * N * (4 + 8) + 8 * (2 * N + 3 * R))
-    return dct + rep["iterations"] * it_bytes(4, 4) + refine * per_ref
+        return dct + rep["iterations"] * it_bytes(8)
+    sweeps = rep["refinements"]
+    return dct + rep["iterations"] * it_bytes(4) + sweeps * (2 * K * N * 12 + 8 * (4 * N + 3 * R))
+
+
+def profiled_traffic(profile_name: str):
+    """DRAM bytes per launch from a committed ncu summary, or None when the
+    kernel source changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", profile_name)
+    src = os.path.join(ROOT, "paper_2309_14584_gb300", "csrc", "fct_device.cu")
+    try:
+        fields = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith(" "))
+        want = fields.get("source_sha256", "").strip()
+        have = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if want and want == have:
+            return int(fields["dram_bytes_per_launch"].strip())
+    except Exception:
+        return None
+    return None
 
 
 def measured_peaks():
@@ -343,7 +366,8 @@ def run_gpu(args):
                        coef_lanes=info["coef_lanes"], parallelism=f"replicas x{world}"),
         "rel_err_vs_oracle": R0["rel_err"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": profiled_traffic("fct_solve_kernel_D6_d10_mixed.txt") if best == "mixed" else None,
                      "kernel": "fct_solve_kernel", "algorithmic_bytes_per_launch": abytes,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth"},
         "e2e": {"value": w.N / R0["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,

@@ -209,6 +209,15 @@ fct_status fct_execute_noalloc(fct_plan plan, const double* samples, double* coe
 /* Report of the plan's last execute (waits for stream). */
 fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);
 
+/*
+ * Diagnostic of the bounded device waits: launches one block that waits at a
+ * barrier meant for two, so the wait can only end by its time limit.
+ * *status_out receives the status the device reported (FCT_ERR_TIMEOUT when
+ * the limit works), *elapsed_s (may be NULL) the kernel's duration.
+ * timeout_s in (0, 10].  Synchronous; allocates and frees a small state.
+ */
+fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* elapsed_s);
+
 /* Release a plan's device memory (synchronises the device first). NULL is OK. */
 fct_status fct_destroy(fct_plan plan);
 

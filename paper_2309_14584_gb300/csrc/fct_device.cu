@@ -1836,3 +1836,48 @@ extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, dou
                 std::string("solver finished with ") + fct_status_string(rep->status));
   return FCT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Diagnostic: a team barrier that cannot complete (one block launched, two
+// expected) must give up after the time limit and report FCT_ERR_TIMEOUT,
+// leaving the context usable.  No fault, trap or unbounded wait is involved.
+// ---------------------------------------------------------------------------
+__global__ void wait_selftest_kernel(LaunchState* ls, unsigned long long timeout_ns) {
+  Team tm;
+  tm.G = 2;  // a partner block that is never launched
+  tm.rank = 0;
+  tm.epoch = 0;
+  tm.bar = &ls->bars[0];
+  tm.err = &ls->err;
+  tm.timeout_ns = timeout_ns;
+  team_sync(tm);
+}
+
+extern "C" fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* elapsed_s) {
+  if (!status_out || !(timeout_s > 0.0) || timeout_s > 10.0)
+    return fail(FCT_ERR_INVALID_ARG, "timeout_s must be in (0, 10]");
+  LaunchState* ls = nullptr;
+  FCT_CUDA(cudaMalloc(&ls, sizeof(LaunchState)));
+  cudaError_t e = cudaMemset(ls, 0, sizeof(LaunchState));
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a);
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32>>>(ls, static_cast<unsigned long long>(timeout_s * 1e9));
+    e = cudaGetLastError();
+  }
+  cudaEventRecord(b);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int err = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, &ls->err, sizeof(int), cudaMemcpyDeviceToHost);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(ls);
+  if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+  *status_out = err;
+  if (elapsed_s) *elapsed_s = ms / 1e3;
+  return FCT_OK;
+}

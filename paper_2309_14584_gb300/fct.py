@@ -105,6 +105,8 @@ SIGNATURES = [
     ("fct_plan_last_report", ctypes.c_int, [_P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
+    ("fct_selftest_wait_timeout", ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_double)]),
     ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, _P, _P, _P,
                                              ctypes.POINTER(ctypes.c_int64)]),
 ]
@@ -273,6 +275,14 @@ def fct_plan_last_report(plan: int, stream=None) -> dict:
     if st != FCT_OK:
         raise FctError(st, lib().fct_last_error().decode())
     return rep.as_dict()
+
+
+def fct_selftest_wait_timeout(timeout_s: float = 0.2) -> tuple[int, float]:
+    """(device status, seconds) of a wait that can only end by its limit."""
+    st = ctypes.c_int()
+    el = ctypes.c_double()
+    _check(lib().fct_selftest_wait_timeout(timeout_s, ctypes.byref(st), ctypes.byref(el)))
+    return st.value, el.value
 
 
 def fct_destroy(plan: int):

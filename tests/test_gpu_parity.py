@@ -299,3 +299,14 @@ def test_batch_of_512_mixed_transforms_equals_alone_and_oracle():
         assert rel(outs[i].cpu().numpy(), ref) <= TOL_MIXED, (w.name, rel(outs[i].cpu().numpy(), ref))
     for p in plans:
         p.close()
+
+
+def test_bounded_wait_times_out_and_context_survives():
+    """A barrier that nothing completes ends by its time limit with
+    FCT_ERR_TIMEOUT; the device stays usable afterwards."""
+    st, el = F.fct.fct_selftest_wait_timeout(0.2)
+    assert st == F.fct.FCT_ERR_TIMEOUT
+    assert 0.15 <= el <= 5.0
+    w = W.config_small_poly()
+    got, _, rep = gpu_run(w, tol=1e-13)
+    assert rep["status"] == 0 and rel(got, w.coeffs_true) <= TOL_FP64
