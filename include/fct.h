@@ -132,6 +132,14 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
                            int K, const int32_t* sizes, const double* nodes,
                            const fct_options* opt);
 
+/*
+ * A second handle on a plan's tables with its own solver workspace, so that
+ * several transforms of the same shape can run at once (e.g. serving slots).
+ * The tables stay on the device until the plan and all its clones are
+ * destroyed.  Synchronous.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_OOM, FCT_ERR_CUDA.
+ */
+fct_status fct_plan_clone(fct_plan* out, fct_plan plan);
+
 /* Plan geometry (host struct). */
 fct_status fct_plan_get_info(fct_plan plan, fct_plan_info* info);
 
@@ -205,6 +213,37 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
  */
 fct_status fct_execute_noalloc(fct_plan plan, const double* samples, double* coeffs, void* stream,
                                fct_report* rep);
+
+/*
+ * Serving with continuous batching.  A server owns one persistent launch whose
+ * teams of blocks take jobs (plan, samples, coeffs) from a ring in host-mapped
+ * memory as soon as they are submitted, so work submitted while other jobs run
+ * overlaps with them on the device; a team that finishes a job takes the next
+ * one.  The launch ends after idle_timeout_s without jobs and is started again
+ * by the next submit or by polling an unclaimed job.
+ *   fct_server_create: block_threads 0/128/256/512 (plans must match),
+ *     team_blocks blocks per team (0 = 16), teams (0 = as many as fit), the
+ *     launch occupies teams * team_blocks co-resident blocks while it runs;
+ *     idle_timeout_s in (0, 1].
+ *   fct_server_submit: samples device double[M], coeffs device double[N]; the
+ *     caller keeps them alive and does not reuse the plan until the job is
+ *     done (one job per plan at a time: a plan owns one workspace).  *ticket
+ *     identifies the job; at most 4096 unfinished jobs (else FCT_ERR_OOM).
+ *   fct_server_poll: *done = 1 and *rep filled once the job has finished.
+ *   fct_server_wait: polls until done or timeout_s (FCT_ERR_TIMEOUT); returns
+ *     the job's status.
+ *   fct_server_destroy: asks the launch to stop, waits for it, frees the server.
+ * Other kernels cannot start on the device while the launch holds all blocks:
+ * size teams to leave room, or prepare inputs before submitting.
+ */
+typedef struct fct_server_s* fct_server;
+fct_status fct_server_create(fct_server* out, int block_threads, int team_blocks, int teams,
+                             double idle_timeout_s);
+fct_status fct_server_submit(fct_server server, fct_plan plan, const double* samples, double* coeffs,
+                             int64_t* ticket);
+fct_status fct_server_poll(fct_server server, int64_t ticket, int* done, fct_report* rep);
+fct_status fct_server_wait(fct_server server, int64_t ticket, double timeout_s, fct_report* rep);
+fct_status fct_server_destroy(fct_server server);
 
 /* Report of the plan's last execute (waits for stream). */
 fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);

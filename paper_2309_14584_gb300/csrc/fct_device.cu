@@ -19,9 +19,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -853,22 +856,22 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       }
       if (!team_sync(tm)) return false;
       // r = b - A x  (FP64)
-      for (int u = tm.rank, k = 0; u < nru; u += tm.G, ++k) {
+      for (int u = tm.rank, ku = 0; u < nru; u += tm.G, ++ku) {
         if (wk < 0) continue;
         int row = 0;
         bool lead = false;
         const double ax =
-            row_gather<double, double>(P, T, P.wcsr, u, k, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
+            row_gather<double, double>(P, T, P.wcsr, u, ku, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
         if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
       }
       if (!team_sync(tm)) return false;
       // g = A^T r (FP64); next inner right-hand side s32 = g / |A^T b|, d = 0
-      for (int c = tm.rank, k = 0; c < ncc; c += tm.G, ++k) {
+      for (int c = tm.rank, kc = 0; c < ncc; c += tm.G, ++kc) {
         int m = 0;
         bool lead = false;
         double t = 0.0;
         if (wk >= 0)
-          t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
+          t = coef_gather<double, double>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
         double part = 0.0;
         if (lead) {
           stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));
@@ -926,7 +929,23 @@ struct SolveArgs {
   LaunchState* ls;
   unsigned long long timeout_ns;
   int smem_bytes;           // dynamic shared memory per block
+  ServerRing* ring;         // serving mode when not null (device view of mapped host memory)
+  unsigned long long idle_ns;  // serving mode: leave after this long without work
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_acquire_sys_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_i32(int* p, int v) {
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 template <int BT>
 __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs a) {
@@ -941,6 +960,49 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
   tm.bar = &a.ls->bars[team];
   tm.err = &a.ls->err;
   tm.timeout_ns = a.timeout_ns;
+  if (a.ring != nullptr) {
+    // Serving: claim published jobs until idle for idle_ns or asked to stop.
+    __shared__ SolveJob s_jobdesc;
+    for (;;) {
+      if (tm.rank == 0 && threadIdx.x == 0) {
+        long long got = -1;
+        const unsigned long long t0 = globaltimer_ns();
+        for (;;) {
+          if (ld_acquire_sys_i32(&a.ring->stop) != 0) break;
+          const unsigned long long tail = ld_acquire_sys_u64(&a.ring->tail);
+          const unsigned int h = ld_volatile_i32(reinterpret_cast<const int*>(&a.ls->queue_head));
+          if (h < tail) {
+            if (atomicCAS(&a.ls->queue_head, h, h + 1u) == h) {
+              got = h;
+              break;
+            }
+            continue;
+          }
+          if (globaltimer_ns() - t0 > a.idle_ns) break;
+          __nanosleep(256);
+        }
+        a.ls->team_job[team] = static_cast<int>(got);
+      }
+      if (!team_sync(tm)) return;
+      if (threadIdx.x == 0) {
+        const int j = ldcg(&a.ls->team_job[team]);
+        s_job = j;
+        if (j >= 0) s_jobdesc = a.ring->slots[j % kRingSize].job;
+      }
+      __syncthreads();
+      const int j = s_job;
+      const SolveJob J = s_jobdesc;
+      __syncthreads();
+      if (j < 0) break;
+      if (!solve_job<BT>(J, tm, red, dsm, a.smem_bytes)) return;
+      if (tm.rank == 0 && threadIdx.x == 0) {
+        __threadfence_system();
+        st_release_sys_i32(&a.ring->slots[j % kRingSize].done, 1);
+      }
+    }
+    team_exit(tm);
+    return;
+  }
   if (a.jobs == nullptr) {
     if (team == 0 && solve_job<BT>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
     return;
@@ -1093,6 +1155,8 @@ struct fct_plan_s {
   // device memory
   char* dmem = nullptr;
   size_t dbytes = 0;
+  std::shared_ptr<char> tables;  // owns dmem of the plan that built the tables (shared by clones)
+  char* wmem = nullptr;          // a clone's own workspace allocation
   DevPlan hp{};
   DevPlan* dp = nullptr;
   LaunchState* ls = nullptr;
@@ -1400,6 +1464,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     return cuda_fail(e, "cudaMalloc(plan)");
   }
   P->dbytes = total;
+  P->tables = std::shared_ptr<char>(P->dmem, [](char* p) { cudaFree(p); });
   {
     size_t off = 0;
     for (auto& pc : pieces) {
@@ -1472,7 +1537,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     chk(cudaDeviceSynchronize());
   }
   if (ue != cudaSuccess || s != FCT_OK) {
-    cudaFree(P->dmem);
+    P->tables.reset();
     delete P;
     return ue != cudaSuccess ? cuda_fail(ue, "plan upload") : s;
   }
@@ -1696,8 +1761,92 @@ fct_status fct_destroy(fct_plan P) {
   if (P->d_stage_in) cudaFree(P->d_stage_in);
   if (P->d_stage_out) cudaFree(P->d_stage_out);
   if (P->djobs) cudaFree(P->djobs);
-  if (P->dmem) cudaFree(P->dmem);
+  if (P->wmem) cudaFree(P->wmem);
+  P->tables.reset();  // frees the table allocation with its last user
   delete P;
+  return FCT_OK;
+}
+
+fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
+  if (!out || !src) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  auto* C = new fct_plan_s();
+  C->device = src->device;
+  C->opt = src->opt;
+  C->H = src->H;
+  C->D = src->D;
+  C->K = src->K;
+  C->N = src->N;
+  C->M = src->M;
+  C->R = src->R;
+  C->dmax = src->dmax;
+  C->sizes = src->sizes;
+  C->tables = src->tables;
+  C->dmem = src->dmem;
+  C->dbytes = src->dbytes;
+  C->hp = src->hp;
+  C->d_sizes = src->d_sizes;
+  C->d_offsets = src->d_offsets;
+  C->d_node_off = src->d_node_off;
+  C->d_node_pos = src->d_node_pos;
+  C->d_support = src->d_support;
+  C->d_ttab = src->d_ttab;
+  C->d_ichunks = src->d_ichunks;
+  C->d_emats = src->d_emats;
+  C->block_threads = src->block_threads;
+  C->grid_blocks = src->grid_blocks;
+  C->max_coresident = src->max_coresident;
+  C->blocks_per_sm = src->blocks_per_sm;
+  C->smem_bytes = src->smem_bytes;
+  C->smem_cap = src->smem_cap;
+  C->ru_first = src->ru_first;
+  C->rowptr_h = src->rowptr_h;
+  // its own workspace, DevPlan copy, launch state and report
+  DevPlan& hp = C->hp;
+  const size_t M = static_cast<size_t>(std::max<int64_t>(C->M, 1)), R = static_cast<size_t>(C->R),
+               N = static_cast<size_t>(C->N);
+  struct Piece {
+    void** dst;
+    size_t bytes;
+  };
+  std::vector<Piece> pieces = {
+      {reinterpret_cast<void**>(&C->dp), sizeof(DevPlan)},
+      {reinterpret_cast<void**>(&C->ls), sizeof(LaunchState)},
+      {reinterpret_cast<void**>(&C->drep), sizeof(fct_report)},
+      {reinterpret_cast<void**>(&hp.y0), sizeof(double) * M},
+      {reinterpret_cast<void**>(&hp.y1), sizeof(double) * M},
+      {reinterpret_cast<void**>(&hp.b), sizeof(double) * R},
+      {reinterpret_cast<void**>(&hp.rres), sizeof(double) * R},
+      {reinterpret_cast<void**>(&hp.q), sizeof(double) * R},
+      {reinterpret_cast<void**>(&hp.sp), sizeof(double2) * N},
+      {reinterpret_cast<void**>(&hp.part_r), sizeof(double) * hp.n_row_units},
+      {reinterpret_cast<void**>(&hp.part_c), sizeof(double) * hp.n_coef_chunks},
+      {reinterpret_cast<void**>(&hp.pr32), sizeof(float) * hp.n_row_units},
+      {reinterpret_cast<void**>(&hp.pc32), sizeof(float) * hp.n_coef_chunks},
+      {reinterpret_cast<void**>(&hp.q32), sizeof(float) * R},
+      {reinterpret_cast<void**>(&hp.sp32), sizeof(float2) * N},
+      {reinterpret_cast<void**>(&hp.dx32), sizeof(float) * N},
+  };
+  size_t total = 0;
+  for (auto& pc : pieces) total += align256(std::max<size_t>(pc.bytes, 1));
+  cudaError_t e = cudaMalloc(&C->wmem, total);
+  if (e != cudaSuccess) {
+    delete C;
+    return cuda_fail(e, "cudaMalloc(plan clone)");
+  }
+  size_t off = 0;
+  for (auto& pc : pieces) {
+    *pc.dst = C->wmem + off;
+    off += align256(std::max<size_t>(pc.bytes, 1));
+  }
+  e = cudaMemset(C->ls, 0, sizeof(LaunchState));
+  if (e == cudaSuccess) e = cudaMemcpy(C->dp, &hp, sizeof(DevPlan), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(C->wmem);
+    delete C;
+    return cuda_fail(e, "plan clone upload");
+  }
+  *out = C;
   return FCT_OK;
 }
 
@@ -1881,3 +2030,169 @@ extern "C" fct_status fct_selftest_wait_timeout(double timeout_s, int* status_ou
   if (elapsed_s) *elapsed_s = ms / 1e3;
   return FCT_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Serving (continuous batching): a persistent launch whose teams take jobs
+// from a ring in host-mapped memory as they are published; a job submitted
+// while others run is picked up by the next team that frees up.  When no job
+// arrives for idle_timeout the launch ends; the next submit (or a wait on an
+// unclaimed job) launches it again.
+// ---------------------------------------------------------------------------
+struct fct_server_s {
+  int device = 0;
+  int block_threads = 256;
+  int team_blocks = 0;
+  int teams = 0;
+  int smem_bytes = 0;
+  unsigned long long idle_ns = 0;
+  unsigned long long timeout_ns = 4000000000ull;
+  ServerRing* h_ring = nullptr;  // host view of the mapped ring
+  ServerRing* d_ring = nullptr;  // device view
+  LaunchState* ls = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  bool launched = false;
+  unsigned long long next = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+fct_status server_ensure_running(fct_server S) {
+  if (S->launched && cudaEventQuery(S->done_ev) == cudaErrorNotReady) return FCT_OK;
+  if (S->launched) {
+    int err = 0;
+    FCT_CUDA(cudaMemcpy(&err, &S->ls->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) return fail(static_cast<fct_status>(err), "serving launch ended with a device-side error");
+  }
+  SolveArgs a{};
+  a.jobs = nullptr;
+  a.njobs = 0;
+  a.team_blocks = S->team_blocks;
+  a.ls = S->ls;
+  a.timeout_ns = S->timeout_ns;
+  a.smem_bytes = S->smem_bytes;
+  a.ring = S->d_ring;
+  a.idle_ns = S->idle_ns;
+  void* kargs[] = {&a};
+  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(S->block_threads), dim3(S->teams * S->team_blocks),
+                                       dim3(S->block_threads), kargs, static_cast<size_t>(S->smem_bytes), S->stream));
+  FCT_CUDA(cudaEventRecord(S->done_ev, S->stream));
+  S->launched = true;
+  return FCT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fct_status fct_server_create(fct_server* out, int block_threads, int team_blocks, int teams, double idle_timeout_s) {
+  if (!out) return fail(FCT_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (block_threads == 0) block_threads = 256;
+  if (block_threads != 128 && block_threads != 256 && block_threads != 512)
+    return fail(FCT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
+  if (!(idle_timeout_s > 0.0) || idle_timeout_s > 1.0) return fail(FCT_ERR_INVALID_ARG, "idle_timeout_s must be in (0, 1]");
+  int dev = 0, nsm = 0, per_sm = 0;
+  FCT_CUDA(cudaGetDevice(&dev));
+  FCT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const void* kfn = solve_kernel_for(block_threads);
+  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block_threads, 0));
+  cudaDeviceProp prop;
+  FCT_CUDA(cudaGetDeviceProperties(&prop, dev));
+  cudaFuncAttributes fa;
+  FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
+  int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / std::max(per_sm, 1)) - 1024 -
+            static_cast<int>(fa.sharedSizeBytes);
+  cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
+  cap = std::max(cap, 0) & ~15;
+  FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  const int coresident = per_sm * nsm;
+  if (team_blocks <= 0) team_blocks = 16;
+  team_blocks = std::min(team_blocks, coresident);
+  const int max_teams = std::min(coresident / team_blocks, kMaxTeams);
+  if (teams <= 0 || teams > max_teams) teams = max_teams;
+  auto* S = new fct_server_s();
+  S->device = dev;
+  S->block_threads = block_threads;
+  S->team_blocks = team_blocks;
+  S->teams = teams;
+  S->smem_bytes = cap;
+  S->idle_ns = static_cast<unsigned long long>(idle_timeout_s * 1e9);
+  cudaError_t e = cudaHostAlloc(&S->h_ring, sizeof(ServerRing), cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess) {
+    std::memset(S->h_ring, 0, sizeof(ServerRing));
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&S->d_ring), S->h_ring, 0);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&S->ls, sizeof(LaunchState));
+  if (e == cudaSuccess) e = cudaMemset(S->ls, 0, sizeof(LaunchState));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&S->done_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    if (S->h_ring) cudaFreeHost(S->h_ring);
+    if (S->ls) cudaFree(S->ls);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    delete S;
+    return cuda_fail(e, "fct_server_create");
+  }
+  *out = S;
+  return FCT_OK;
+}
+
+fct_status fct_server_submit(fct_server S, fct_plan P, const double* samples, double* coeffs, int64_t* ticket) {
+  if (!S || !P || !samples || !coeffs || !ticket) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  if (P->block_threads != S->block_threads) return fail(FCT_ERR_INVALID_ARG, "plan block_threads differs from the server's");
+  std::lock_guard<std::mutex> lk(S->mu);
+  const unsigned long long j = S->next;
+  ServerSlot& slot = S->h_ring->slots[j % kRingSize];
+  if (j >= static_cast<unsigned long long>(kRingSize) && __atomic_load_n(&slot.done, __ATOMIC_ACQUIRE) == 0)
+    return fail(FCT_ERR_OOM, "serving ring full: the job submitted 4096 tickets ago has not finished");
+  slot.job = make_job(P, samples, coeffs, &S->d_ring->slots[j % kRingSize].rep);
+  std::memset(&slot.rep, 0, sizeof(slot.rep));
+  __atomic_store_n(&slot.done, 0, __ATOMIC_RELAXED);
+  __atomic_store_n(&S->h_ring->tail, j + 1, __ATOMIC_RELEASE);  // publishes the slot
+  S->next = j + 1;
+  *ticket = static_cast<int64_t>(j);
+  return server_ensure_running(S);
+}
+
+fct_status fct_server_poll(fct_server S, int64_t ticket, int* done, fct_report* rep) {
+  if (!S || !done || ticket < 0) return fail(FCT_ERR_INVALID_ARG, "bad argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (static_cast<unsigned long long>(ticket) >= S->next) return fail(FCT_ERR_INVALID_ARG, "unknown ticket");
+  ServerSlot& slot = S->h_ring->slots[ticket % kRingSize];
+  *done = __atomic_load_n(&slot.done, __ATOMIC_ACQUIRE);
+  if (*done) {
+    if (rep) *rep = slot.rep;
+    return FCT_OK;
+  }
+  // a job published just as the launch went idle is picked up by a new launch
+  return server_ensure_running(S);
+}
+
+fct_status fct_server_wait(fct_server S, int64_t ticket, double timeout_s, fct_report* rep) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    int done = 0;
+    fct_status st = fct_server_poll(S, ticket, &done, rep);
+    if (st != FCT_OK) return st;
+    if (done) return rep ? static_cast<fct_status>(rep->status) : FCT_OK;
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el > timeout_s) return fail(FCT_ERR_TIMEOUT, "fct_server_wait: job not finished in time");
+    std::this_thread::yield();
+  }
+}
+
+fct_status fct_server_destroy(fct_server S) {
+  if (!S) return FCT_OK;
+  __atomic_store_n(&S->h_ring->stop, 1, __ATOMIC_RELEASE);
+  cudaStreamSynchronize(S->stream);
+  cudaEventDestroy(S->done_ev);
+  cudaStreamDestroy(S->stream);
+  cudaFree(S->ls);
+  cudaFreeHost(S->h_ring);
+  delete S;
+  return FCT_OK;
+}
+
+}  // extern "C"

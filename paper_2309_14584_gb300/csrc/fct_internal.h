@@ -119,6 +119,25 @@ struct LaunchState {
   TeamBarrier bars[kMaxTeams];
 };
 
+// Serving ring in host-mapped memory: the host publishes jobs (slot then
+// tail, release), team leaders claim them through LaunchState::queue_head,
+// and each finished job gets its report and done flag (system-scope release).
+constexpr int kRingSize = 4096;
+
+struct ServerSlot {
+  SolveJob job;
+  fct_report rep;
+  int done;
+  int pad[15];
+};
+
+struct ServerRing {
+  unsigned long long tail;  // jobs published so far (monotonic)
+  int stop;                 // host asks the serving kernel to leave
+  int pad[13];
+  ServerSlot slots[kRingSize];
+};
+
 // Host-side alias tables of a plan (also exported by fct_alias_tables_host).
 // Rows are numbered grid by grid, nonempty bins in ascending bin order;
 // device_row_order() renumbers them for the solver.

@@ -105,6 +105,13 @@ SIGNATURES = [
     ("fct_plan_last_report", ctypes.c_int, [_P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
+    ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
+    ("fct_server_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double]),
+    ("fct_server_submit", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
+    ("fct_server_poll", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(fct_report)]),
+    ("fct_server_wait", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(fct_report)]),
+    ("fct_server_destroy", ctypes.c_int, [_P]),
     ("fct_selftest_wait_timeout", ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(ctypes.c_double)]),
     ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, _P, _P, _P,
@@ -285,6 +292,45 @@ def fct_selftest_wait_timeout(timeout_s: float = 0.2) -> tuple[int, float]:
     return st.value, el.value
 
 
+def fct_plan_clone(plan: int) -> int:
+    h = _P()
+    _check(lib().fct_plan_clone(ctypes.byref(h), plan))
+    return h.value
+
+
+def fct_server_create(block_threads: int = 0, team_blocks: int = 0, teams: int = 0,
+                      idle_timeout_s: float = 0.05) -> int:
+    h = _P()
+    _check(lib().fct_server_create(ctypes.byref(h), block_threads, team_blocks, teams, idle_timeout_s))
+    return h.value
+
+
+def fct_server_submit(server: int, plan: int, samples, coeffs) -> int:
+    t = ctypes.c_int64()
+    _check(lib().fct_server_submit(server, plan, _ptr(samples), _ptr(coeffs), ctypes.byref(t)))
+    return t.value
+
+
+def fct_server_poll(server: int, ticket: int) -> dict | None:
+    done = ctypes.c_int()
+    rep = fct_report()
+    _check(lib().fct_server_poll(server, ticket, ctypes.byref(done), ctypes.byref(rep)))
+    return rep.as_dict() if done.value else None
+
+
+def fct_server_wait(server: int, ticket: int, timeout_s: float = 60.0) -> dict:
+    rep = fct_report()
+    st = lib().fct_server_wait(server, ticket, timeout_s, ctypes.byref(rep))
+    if st != FCT_OK:
+        raise FctError(st, lib().fct_last_error().decode() + f" (report {rep.as_dict()})")
+    return rep.as_dict()
+
+
+def fct_server_destroy(server: int):
+    if server:
+        _check(lib().fct_server_destroy(server))
+
+
 def fct_destroy(plan: int):
     if plan:
         _check(lib().fct_destroy(plan))
@@ -324,6 +370,15 @@ class Plan:
     @property
     def M(self):
         return self.info["M"]
+
+    def clone(self) -> "Plan":
+        """Another handle on the same device tables with its own workspace."""
+        c = Plan.__new__(Plan)
+        c.support, c.sizes = self.support, self.sizes
+        c.handle = fct_plan_clone(self.handle)
+        c.info = fct_plan_get_info(c.handle)
+        c.offsets = self.offsets
+        return c
 
     def sample(self, family, params, samples, stream=None):
         fct_sample(self.handle, family, params, samples, stream)

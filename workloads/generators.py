@@ -217,3 +217,28 @@ def config_batch(seed: int = 4, B: int = 512) -> list:
         out.append(make_workload(f"b{t}_D{D}_d{d}_Knom{k_nominal}", seed * 1_000_003 + t, D, d, 3 * D, 1, d + 1,
                                  FAMILY_POLY_GAUSSCOS, tol=1e-12, precision="mixed"))
     return out
+
+
+def serving_shapes(seed: int = 5, dims=range(2, 21), nmin: int = 1000, nmax: int = 100000) -> list:
+    """One plan shape per dimension D: total degree d drawn uniformly from the
+    degrees whose support size C(D+d, d) lies in [nmin, nmax]; L = 3D grids
+    with sizes {1..d+1} (Algorithm 1).  Targets are filled in per request."""
+    g = stream(seed, "batch")
+    out = []
+    for D in dims:
+        valid = [d for d in range(1, 2000) if nmin <= math.comb(D + d, d) <= nmax]
+        d = int(valid[int(g.integers(0, len(valid)))])
+        out.append(make_workload(f"serve_D{D}_d{d}", seed * 1_000_003 + D, D, d, 3 * D, 1, d + 1,
+                                 FAMILY_GAUSSCOS, tol=1e-12, precision="mixed"))
+    return out
+
+
+def serving_requests(seed: int, n: int, rate: float, n_shapes: int, poly_fraction: float = 0.05):
+    """Poisson arrivals at `rate` req/s: list of (arrival_s, shape index,
+    is_polynomial, parameter seed)."""
+    g = stream(seed, "arrivals")
+    t = np.cumsum(g.exponential(1.0 / rate, n))
+    shape = g.integers(0, n_shapes, n)
+    poly = g.random(n) < poly_fraction
+    pseed = g.integers(0, 2**31 - 1, n)
+    return [(float(t[i]), int(shape[i]), bool(poly[i]), int(pseed[i])) for i in range(n)]
