@@ -15,11 +15,13 @@ What it computes (Algorithm 3, Sec. 3.4): for an L-grid of K tensor grids,
                from the fold relation, the extrema-grid analogue of
                Lemma (lem:aliasing) / Eq. (aliasing_matrix_nd_diff))
     c* = argmin_c || b - A c ||_2      (the least-squares problem of Sec. 3.4)
+and the grid-count selection of Algorithm 2 (Sec. 3.3): grids are appended
+in a given candidate order until kappa(A) <= kappa0.
 
 Readings of the paper this oracle follows (each also listed in the design doc):
   * grid: Chebyshev extrema x_j = cos(pi j / (n-1)), j = 0..n-1, with a DCT-I
     per axis and an unsigned fold (the paper's first-kind grid / DCT-II form
-    is the ``*_first_kind`` family below);
+    is not part of this module);
   * normalisation: b holds the exact Chebyshev coefficients of the grid
     interpolant, so A has unit entries times single-point weights;
   * an axis with one point samples at a given node xi and contributes the
@@ -384,14 +386,31 @@ def fct(support, sizes, nodes, samples, method: str = "auto", tol: float = 1e-15
 
 
 def condition_number(A) -> float:
-    """kappa(A) = sigma_max / sigma_min from the eigenvalues of A^T A (dense;
-    N up to ~1e4).  Returns inf when A^T A is singular to working precision."""
-    AtA = (A.T @ A)
-    AtA = AtA.toarray() if sp.issparse(AtA) else AtA
-    ev = np.linalg.eigvalsh(AtA)
-    if ev[0] <= ev[-1] * 1e-28:
+    """kappa(A) = sigma_max / sigma_min, the singular values of the dense A
+    (N up to a few thousand).  Returns inf when A has fewer rows than columns
+    or sigma_min is below rounding level (R * eps * sigma_max)."""
+    A = A.toarray() if sp.issparse(A) else np.asarray(A, dtype=np.float64)
+    if A.shape[0] < A.shape[1]:
         return math.inf
-    return math.sqrt(ev[-1] / ev[0])
+    sv = np.linalg.svd(A, compute_uv=False)
+    if sv[-1] <= sv[0] * A.shape[0] * np.finfo(np.float64).eps:
+        return math.inf
+    return float(sv[0] / sv[-1])
+
+
+def construct_alias_system(support, cand_sizes, cand_nodes, kappa0: float = 1e4):
+    """Algorithm 2 (Sec. 3.3): starting from no grids, append the next grid of
+    the candidate sequence (each one an Algorithm 1 draw, passed in) until the
+    stacked alias matrix has kappa(A) <= kappa0; a rank-deficient A has
+    kappa = inf.  Returns ``(L, kappa(A))`` for the first L grids, or
+    ``(None, kappa)`` when every candidate has been used."""
+    cand_sizes = np.asarray(cand_sizes)
+    kappa = math.inf
+    for L in range(1, cand_sizes.shape[0] + 1):
+        kappa = condition_number(AliasSystem(support, cand_sizes[:L], np.asarray(cand_nodes)[:L]).A)
+        if kappa <= kappa0:
+            return L, kappa
+    return None, kappa
 
 
 def numerical_rank(A, rtol: float = 1e-10) -> int:

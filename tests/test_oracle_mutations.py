@@ -1,6 +1,8 @@
 """Plant plausible mistakes in the oracle (CPU only) and check that at least
 one pin in test_oracle_pins fails for each.  A pin set that let one of these
 through would not pin the oracle."""
+import math
+
 import numpy as np
 import pytest
 
@@ -83,6 +85,23 @@ def _cgls_wrong_sign(A, b, tol=1e-15, maxit=100000):
     return x, it, 0.0
 
 
+_orig_cond = O.condition_number
+_orig_construct = O.construct_alias_system
+
+
+def _cond_squared(A):
+    k = _orig_cond(A)
+    return k * k
+
+
+def _construct_one_late(support, cand_sizes, cand_nodes, kappa0=1e4):
+    # tests the bound only after appending the next grid
+    L, _ = _orig_construct(support, cand_sizes, cand_nodes, kappa0)
+    if L is None or L >= len(cand_sizes):
+        return L, math.inf
+    return L + 1, _orig_cond(O.AliasSystem(support, cand_sizes[:L + 1], cand_nodes[:L + 1]).A)
+
+
 MUTATIONS = [
     ("fold_off_by_one", "fold", _fold_off_by_one, lambda: P.test_fold_identity_exhaustive()),
     ("fold_off_by_one_recovery", "fold", _fold_off_by_one,
@@ -97,6 +116,9 @@ MUTATIONS = [
     ("T_recurrence_bad", "chebyshev_T_table", _T_table_bad,
      lambda: P.test_chebyshev_definition_recurrence_and_library_agree()),
     ("cgls_wrong_sign", "cgls", _cgls_wrong_sign, lambda: P.test_solver_tiers_agree_and_are_optimal()),
+    ("condition_squared", "condition_number", _cond_squared, lambda: P.test_condition_number_closed_forms()),
+    ("alg2_one_late", "construct_alias_system", _construct_one_late,
+     lambda: P.test_alg2_returns_the_first_prefix_within_bound(6.0)),
 ]
 
 

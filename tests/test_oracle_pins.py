@@ -304,3 +304,76 @@ def test_workload_shapes():
     assert w.M == int(np.prod(w.sizes, axis=1).sum())
     w2 = W.config_d6_gausscos()
     assert (w2.N, w2.K) == (8008, 18)
+
+
+# ---------------------------------------------------------------- Algorithm 2
+def _stacked_bruteforce(support, sizes, nodes):
+    """Alias matrices of the grids from the definition (every bin, empty rows
+    included: zero rows change no singular value)."""
+    return np.vstack([O.alias_matrix_grid_bruteforce(support, sizes[l], nodes[l]) for l in range(len(sizes))])
+
+
+def _kappa_eig(A):
+    ev = np.linalg.eigvalsh(A.T @ A)
+    return math.sqrt(ev[-1] / ev[0]) if ev[0] > 0 else math.inf
+
+
+def test_condition_number_closed_forms():
+    """kappa of a diagonal matrix is max/min of |d|; of an orthogonal one, 1;
+    a wide matrix is rank-deficient; for a moderately conditioned alias
+    matrix it equals the eigenvalue route sqrt(lambda_max/lambda_min) of A^T A."""
+    d = np.array([3.0, -0.5, 2.0, 0.25])
+    assert O.condition_number(np.diag(d)) == pytest.approx(12.0, rel=1e-14)
+    q, _ = np.linalg.qr(W.stream(11, "probe").standard_normal((7, 7)))
+    assert O.condition_number(q) == pytest.approx(1.0, rel=1e-13)
+    assert O.condition_number(np.ones((2, 3))) == math.inf
+    assert O.condition_number(np.outer(np.arange(1.0, 6.0), np.arange(1.0, 4.0))) == math.inf
+    sup = W.total_degree_support(3, 4)
+    sizes, nodes = W.l_grid(12, sup.shape[0], 3, 9, 2, 5)
+    A = _stacked_bruteforce(sup, sizes, nodes)
+    k = _kappa_eig(A)
+    assert 1.0 < k < 1e4
+    assert O.condition_number(O.AliasSystem(sup, sizes, nodes).A) == pytest.approx(k, rel=1e-9)
+
+
+def test_alg2_single_full_grid_stops_at_one():
+    """One axis with n = d + 1 extrema points resolves every degree without
+    collision: A is the identity, kappa = 1 and Algorithm 2 stops at L = 1."""
+    d = 9
+    sup = np.arange(d + 1, dtype=np.uint16).reshape(-1, 1)
+    sizes = np.array([[d + 1], [3], [4]], dtype=np.int32)
+    L, kappa = O.construct_alias_system(sup, sizes, np.ones((3, 1)), kappa0=1.0 + 1e-12)
+    assert L == 1 and kappa == pytest.approx(1.0, abs=1e-12)
+
+
+def test_alg2_single_point_grids_need_N_grids():
+    """Grids of one point each contribute one row: below N grids A is
+    rank-deficient (kappa = inf), and at generic points exactly N grids give a
+    nonsingular square A, so Algorithm 2 with a loose bound returns L = N."""
+    D, d = 2, 2
+    sup = W.total_degree_support(D, d)
+    N = sup.shape[0]
+    K = N + 3
+    sizes = np.ones((K, D), dtype=np.int32)
+    nodes = np.cos(np.pi * W.stream(13, "nodes").random((K, D)))
+    L, kappa = O.construct_alias_system(sup, sizes, nodes, kappa0=1e12)
+    assert L == N
+    # the same matrix from the definition: T_{m1}(x1) T_{m2}(x2) at the N points
+    V = np.array([[O.chebyshev_T(int(m[0]), nodes[l, 0]) * O.chebyshev_T(int(m[1]), nodes[l, 1]) for m in sup]
+                  for l in range(N)])
+    sv = np.linalg.svd(V, compute_uv=False)
+    assert kappa == pytest.approx(sv[0] / sv[-1], rel=1e-9)
+
+
+@pytest.mark.parametrize("kappa0", [4.5, 6.0, 7.3, 1e3])
+def test_alg2_returns_the_first_prefix_within_bound(kappa0):
+    """Algorithm 2's stopping rule, checked on matrices built from the
+    definition: kappa(first L grids) <= kappa0 < kappa(first L-1 grids)."""
+    D, d = 3, 4
+    sup = W.total_degree_support(D, d)
+    sizes, nodes = W.l_grid(14, sup.shape[0], D, 24, 2, d + 1)
+    L, kappa = O.construct_alias_system(sup, sizes, nodes, kappa0)
+    assert L is not None
+    assert _kappa_eig(_stacked_bruteforce(sup, sizes[:L], nodes[:L])) <= kappa0 * (1 + 1e-9)
+    if L > 1:
+        assert _kappa_eig(_stacked_bruteforce(sup, sizes[:L - 1], nodes[:L - 1])) > kappa0 * (1 - 1e-9)

@@ -36,6 +36,7 @@ _PURPOSE = {
     "nodes": 4,      # single-point node positions
     "batch": 5,      # per-transform shapes inside a batch
     "arrivals": 6,   # serving arrival process
+    "probe": 7,      # start vectors of condition probes and test matrices
 }
 
 
