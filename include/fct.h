@@ -257,6 +257,23 @@ fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);
  */
 fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* elapsed_s);
 
+/*
+ * Condition estimate for Algorithm 2 (Sec. 3.3: grids are appended while
+ * kappa(A) exceeds a bound).  CG on A^T A is the Lanczos process: this runs
+ * `iterations` FP64 CG iterations on A^T A z = start (start: device double[N],
+ * a random vector reaches every eigenvector, including a null space of A;
+ * work: device double[N], receives the iterate), reads back the CG
+ * coefficients, builds the Lanczos tridiagonal and bisects its extreme
+ * eigenvalues.  *lambda_min, *lambda_max estimate sigma_min^2 and
+ * sigma_max^2 of A from inside; *kappa = sqrt(lambda_max / lambda_min) is a
+ * lower bound on kappa(A) that tightens as iterations grow (the CG
+ * coefficients carry FP32-reduced norms, so the estimate resolves kappa up to
+ * about 1e3); *used = iterations recorded (fewer when the iteration breaks
+ * down).  Outputs other than kappa may be NULL.  Synchronous.
+ */
+fct_status fct_plan_condition(fct_plan plan, const double* start, double* work, int iterations,
+                              double* kappa, double* lambda_min, double* lambda_max, int* used, void* stream);
+
 /* Release a plan's device memory (synchronises the device first). NULL is OK. */
 fct_status fct_destroy(fct_plan plan);
 

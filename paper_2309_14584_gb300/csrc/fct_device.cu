@@ -624,7 +624,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     __syncthreads();
   };
   int ctl = 0;
-  for (;;) {
+  for (int pass = 0;; ++pass) {
     // ================= phase A: q = A s + beta A p
     {
       auto gather_a = [&](int u, int k, V* as, V* ap, int* row, bool* lead) {
@@ -718,6 +718,8 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           else al = gam / dl;
           sh_ab[1] = al;
           sh_ctl[0] = cc;
+          if (P.hist != nullptr && tm.rank == 0 && cc == 0 && pass < P.hist_cap)
+            P.hist[pass] = make_float2(al, first ? 0.0f : sh_ab[0]);
         }
       }
       __syncthreads();
@@ -780,38 +782,55 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
   const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units;
   const int wk = static_cast<int>(threadIdx.x) - 32;
   const int nce = (P.N + BT - 1) / BT;  // elementwise units over coefficients
-  // ---- full DCT-I axis passes
-  for (int pass = 0; pass < P.npass; ++pass) {
-    const int c0 = __ldg(P.pass_chunk_off + pass), c1 = __ldg(P.pass_chunk_off + pass + 1);
-    for (int c = c0 + tm.rank; c < c1; c += tm.G) dct_unit<BT>(P, T.mats, J.samples, P.dct_chunks[c]);
+  if (P.s_init != nullptr) {
+    // ---- condition probe: x = 0, s = s_init
+    for (int u = tm.rank; u < ncc; u += tm.G) {
+      const int m = u * BT + threadIdx.x;
+      double part = 0.0;
+      if (m < P.N) {
+        const double v = __ldg(P.s_init + m);
+        stcg(P.sp + m, make_double2(v, 0.0));
+        stcg(J.coeffs + m, 0.0);
+        part = v * v;
+      }
+      part = block_sum<BT>(part, red);
+      if (threadIdx.x == 0) stcg(P.part_c + u, part);
+    }
+    if (!team_sync(tm)) return false;
+  } else {
+    // ---- full DCT-I axis passes
+    for (int pass = 0; pass < P.npass; ++pass) {
+      const int c0 = __ldg(P.pass_chunk_off + pass), c1 = __ldg(P.pass_chunk_off + pass + 1);
+      for (int c = c0 + tm.rank; c < c1; c += tm.G) dct_unit<BT>(P, T.mats, J.samples, P.dct_chunks[c]);
+      if (!team_sync(tm)) return false;
+    }
+    // ---- last pass at the nonempty bins -> b ; x = 0
+    for (int u = tm.rank; u < nre + nce; u += tm.G) {
+      if (u < nre) {
+        const int row = u * BT + threadIdx.x;
+        if (row < P.R) stcg(P.b + row, dct_final_row(P, T.mats, J.samples, row));
+      } else {
+        const int m = (u - nre) * BT + threadIdx.x;
+        if (m < P.N) stcg(J.coeffs + m, 0.0);
+      }
+    }
+    if (!team_sync(tm)) return false;
+    // ---- s = A^T b, gamma0 = |A^T b|^2
+    for (int c = tm.rank, k = 0; c < ncc; c += tm.G, ++k) {
+      int m = 0;
+      bool lead = false;
+      double t = 0.0;
+      if (wk >= 0) t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
+      double part = 0.0;
+      if (lead) {
+        stcg(P.sp + m, make_double2(t, 0.0));
+        part = t * t;
+      }
+      part = block_sum<BT>(part, red);
+      if (threadIdx.x == 0) stcg(P.part_c + c, part);
+    }
     if (!team_sync(tm)) return false;
   }
-  // ---- last pass at the nonempty bins -> b ; x = 0
-  for (int u = tm.rank; u < nre + nce; u += tm.G) {
-    if (u < nre) {
-      const int row = u * BT + threadIdx.x;
-      if (row < P.R) stcg(P.b + row, dct_final_row(P, T.mats, J.samples, row));
-    } else {
-      const int m = (u - nre) * BT + threadIdx.x;
-      if (m < P.N) stcg(J.coeffs + m, 0.0);
-    }
-  }
-  if (!team_sync(tm)) return false;
-  // ---- s = A^T b, gamma0 = |A^T b|^2
-  for (int c = tm.rank, k = 0; c < ncc; c += tm.G, ++k) {
-    int m = 0;
-    bool lead = false;
-    double t = 0.0;
-    if (wk >= 0) t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
-    double part = 0.0;
-    if (lead) {
-      stcg(P.sp + m, make_double2(t, 0.0));
-      part = t * t;
-    }
-    part = block_sum<BT>(part, red);
-    if (threadIdx.x == 0) stcg(P.part_c + c, part);
-  }
-  if (!team_sync(tm)) return false;
   const double gamma0 = team_sum<BT>(P.part_c, ncc, red);
 
   int status = FCT_OK, iters = 0, refines = 0;
@@ -1162,6 +1181,8 @@ struct fct_plan_s {
   LaunchState* ls = nullptr;
   fct_report* drep = nullptr;
   SolveJob* djobs = nullptr;     // batch job array (grown on demand)
+  char* d_hist_block = nullptr;  // condition estimate: DevPlan copy + coefficient history
+  int hist_cap = 0;
   int djobs_cap = 0;
   // sampler
   int32_t* d_sizes = nullptr;
@@ -1761,6 +1782,7 @@ fct_status fct_destroy(fct_plan P) {
   if (P->d_stage_in) cudaFree(P->d_stage_in);
   if (P->d_stage_out) cudaFree(P->d_stage_out);
   if (P->djobs) cudaFree(P->djobs);
+  if (P->d_hist_block) cudaFree(P->d_hist_block);
   if (P->wmem) cudaFree(P->wmem);
   P->tables.reset();  // frees the table allocation with its last user
   delete P;
@@ -2196,3 +2218,116 @@ fct_status fct_server_destroy(fct_server S) {
 }
 
 }  // extern "C"
+
+
+// ---------------------------------------------------------------------------
+// Condition estimate for Algorithm 2's test kappa(A) <= kappa0: CG on A^T A is
+// the Lanczos process, so its coefficients give the Lanczos tridiagonal T_k
+//   T[j][j] = 1/alpha_j + beta_j/alpha_{j-1},  T[j][j+1] = sqrt(beta_{j+1})/alpha_j,
+// whose extreme eigenvalues (Ritz values) approach those of A^T A from inside:
+// sqrt(lambda_max / lambda_min) is a lower bound on kappa(A) that tightens
+// with k.
+// ---------------------------------------------------------------------------
+namespace {
+
+// number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm)
+int sturm_below(const std::vector<double>& d, const std::vector<double>& e, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    const double e2 = i > 0 ? e[i - 1] * e[i - 1] : 0.0;
+    q = (d[i] - x) - (i > 0 ? e2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+
+void tridiag_extremes(const std::vector<double>& d, const std::vector<double>& e, double* lmin, double* lmax) {
+  const size_t k = d.size();
+  double lo = d[0], hi = d[0];
+  for (size_t i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  double a = lo, b = hi;  // smallest: count(x) >= 1
+  for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+    const double m = 0.5 * (a + b);
+    if (sturm_below(d, e, m) >= 1) b = m; else a = m;
+  }
+  *lmin = 0.5 * (a + b);
+  a = lo;
+  b = hi;  // largest: count(x) >= k
+  for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+    const double m = 0.5 * (a + b);
+    if (sturm_below(d, e, m) >= static_cast<int>(k)) b = m; else a = m;
+  }
+  *lmax = 0.5 * (a + b);
+}
+
+}  // namespace
+
+extern "C" fct_status fct_plan_condition(fct_plan P, const double* start, double* work, int iterations,
+                                         double* kappa, double* lambda_min, double* lambda_max, int* used,
+                                         void* stream) {
+  if (!P || !start || !work || !kappa) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  if (iterations < 2 || iterations > 100000) return fail(FCT_ERR_INVALID_ARG, "iterations must be in [2, 100000]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (P->hist_cap < iterations) {
+    if (P->d_hist_block) {
+      FCT_CUDA(cudaStreamSynchronize(st));
+      cudaFree(P->d_hist_block);
+      P->d_hist_block = nullptr;
+      P->hist_cap = 0;
+    }
+    FCT_CUDA(cudaMalloc(&P->d_hist_block, align256(sizeof(DevPlan)) + sizeof(float2) * iterations));
+    P->hist_cap = iterations;
+  }
+  DevPlan hp = P->hp;
+  hp.s_init = start;
+  hp.hist = reinterpret_cast<float2*>(P->d_hist_block + align256(sizeof(DevPlan)));
+  hp.hist_cap = iterations;
+  DevPlan* dplan = reinterpret_cast<DevPlan*>(P->d_hist_block);
+  FCT_CUDA(cudaMemcpyAsync(dplan, &hp, sizeof(DevPlan), cudaMemcpyHostToDevice, st));
+  FCT_CUDA(cudaMemsetAsync(hp.hist, 0, sizeof(float2) * iterations, st));
+  SolveArgs a{};
+  a.single = make_job(P, nullptr, work, P->drep);
+  a.single.plan = dplan;
+  a.single.precision = FCT_FP64;
+  a.single.max_iter = iterations;
+  a.single.tol = 0.0;
+  a.jobs = nullptr;
+  a.njobs = 1;
+  a.team_blocks = P->grid_blocks;
+  a.ls = P->ls;
+  a.timeout_ns = timeout_ns(P);
+  a.smem_bytes = P->smem_bytes;
+  fct_status s = launch_solve(P, a, P->grid_blocks, st);
+  if (s != FCT_OK) return s;
+  fct_report rep;
+  s = read_report(P, P->drep, st, &rep);
+  if (s != FCT_OK && s != FCT_ERR_NOCONV) return s;
+  std::vector<float2> h(iterations);
+  FCT_CUDA(cudaMemcpy(h.data(), hp.hist, sizeof(float2) * iterations, cudaMemcpyDeviceToHost));
+  int k = std::min(rep.iterations, iterations);
+  for (int j = 0; j < k; ++j)
+    if (!(h[j].x > 0.0f) || !std::isfinite(h[j].x) || !(h[j].y >= 0.0f) || !std::isfinite(h[j].y)) {
+      k = j;
+      break;
+    }
+  if (k < 1) return fail(FCT_ERR_INVALID_ARG, "the probe recorded no iteration (zero start vector?)");
+  std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+  for (int j = 0; j < k; ++j) {
+    const double al = h[j].x;
+    d[j] = 1.0 / al + (j > 0 ? static_cast<double>(h[j].y) / static_cast<double>(h[j - 1].x) : 0.0);
+    if (j + 1 < k) e[j] = std::sqrt(static_cast<double>(h[j + 1].y)) / al;
+  }
+  double lmin = 0.0, lmax = 0.0;
+  tridiag_extremes(d, e, &lmin, &lmax);
+  if (lambda_min) *lambda_min = lmin;
+  if (lambda_max) *lambda_max = lmax;
+  if (used) *used = k;
+  *kappa = lmin > 0.0 ? std::sqrt(lmax / lmin) : INFINITY;
+  return FCT_OK;
+}

@@ -85,6 +85,13 @@ struct DevPlan {
   float* q32;                // [R]
   float2* sp32;              // [N] {s, p} of the inner FP32 solve
   float* dx32;               // [N]
+  // condition estimate: when set, the FP64 solve starts from s = s_init (no
+  // DCT, no b) and block 0 records (alpha_k, beta_k) of every CG iteration,
+  // the Lanczos coefficients of A^T A for the start vector s_init
+  const double* s_init;      // [N] or nullptr
+  float2* hist;              // [hist_cap] or nullptr
+  int32_t hist_cap;
+  int32_t pad_hist;
 };
 
 // One transform of a launch.

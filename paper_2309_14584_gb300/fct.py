@@ -106,6 +106,9 @@ SIGNATURES = [
     ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
     ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
+    ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int), _P]),
     ("fct_server_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_double]),
     ("fct_server_submit", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int64)]),
@@ -290,6 +293,16 @@ def fct_selftest_wait_timeout(timeout_s: float = 0.2) -> tuple[int, float]:
     el = ctypes.c_double()
     _check(lib().fct_selftest_wait_timeout(timeout_s, ctypes.byref(st), ctypes.byref(el)))
     return st.value, el.value
+
+
+def fct_plan_condition(plan: int, start, work, iterations: int = 200, stream=None) -> dict:
+    """Lanczos estimate of kappa(A) from `iterations` CG iterations on
+    A^T A z = start (device double[N]; work: device double[N] scratch)."""
+    k, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    used = ctypes.c_int()
+    _check(lib().fct_plan_condition(plan, _ptr(start), _ptr(work), iterations, ctypes.byref(k), ctypes.byref(lo),
+                                    ctypes.byref(hi), ctypes.byref(used), _stream(stream)))
+    return {"kappa": k.value, "lambda_min": lo.value, "lambda_max": hi.value, "iterations": used.value}
 
 
 def fct_plan_clone(plan: int) -> int:

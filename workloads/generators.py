@@ -220,18 +220,26 @@ def config_batch(seed: int = 4, B: int = 512) -> list:
     return out
 
 
-def serving_shapes(seed: int = 5, dims=range(2, 21), nmin: int = 1000, nmax: int = 100000) -> list:
+def serving_shapes(seed: int = 5, dims=range(2, 21), nmin: int = 1000, nmax: int = 100000,
+                   grids_per_dim: int = 3) -> list:
     """One plan shape per dimension D: total degree d drawn uniformly from the
     degrees whose support size C(D+d, d) lies in [nmin, nmax]; L = 3D grids
-    with sizes {1..d+1} (Algorithm 1).  Targets are filled in per request."""
+    (grids_per_dim * D) with sizes {1..d+1} (Algorithm 1).  Grid draws are
+    sequential, so a larger grids_per_dim extends the same sequence: it is the
+    candidate list for Algorithm 2.  Targets are filled in per request."""
     g = stream(seed, "batch")
     out = []
     for D in dims:
         valid = [d for d in range(1, 2000) if nmin <= math.comb(D + d, d) <= nmax]
         d = int(valid[int(g.integers(0, len(valid)))])
-        out.append(make_workload(f"serve_D{D}_d{d}", seed * 1_000_003 + D, D, d, 3 * D, 1, d + 1,
+        out.append(make_workload(f"serve_D{D}_d{d}", seed * 1_000_003 + D, D, d, grids_per_dim * D, 1, d + 1,
                                  FAMILY_GAUSSCOS, tol=1e-12, precision="mixed"))
     return out
+
+
+def first_grids(w: Workload, L: int) -> Workload:
+    """The same workload on the first L grids of its L-grid."""
+    return dataclasses.replace(w, name=f"{w.name}_L{L}", sizes=w.sizes[:L].copy(), nodes=w.nodes[:L].copy())
 
 
 def serving_requests(seed: int, n: int, rate: float, n_shapes: int, poly_fraction: float = 0.05):
