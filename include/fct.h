@@ -219,8 +219,9 @@ fct_status fct_execute_noalloc(fct_plan plan, const double* samples, double* coe
  * teams of blocks take jobs (plan, samples, coeffs) from a ring in host-mapped
  * memory as soon as they are submitted, so work submitted while other jobs run
  * overlaps with them on the device; a team that finishes a job takes the next
- * one.  The launch ends after idle_timeout_s without jobs and is started again
- * by the next submit or by polling an unclaimed job.
+ * one.  Every team stays while any job runs; the launch ends once no job has
+ * run for idle_timeout_s, and is started again by the next submit or by
+ * polling an unclaimed job.
  *   fct_server_create: block_threads 0/128/256/512 (plans must match),
  *     team_blocks blocks per team (0 = 16), teams (0 = as many as fit), the
  *     launch occupies teams * team_blocks co-resident blocks while it runs;

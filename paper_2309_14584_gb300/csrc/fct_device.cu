@@ -988,16 +988,26 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
         const unsigned long long t0 = globaltimer_ns();
         for (;;) {
           if (ld_acquire_sys_i32(&a.ring->stop) != 0) break;
+          if (ld_volatile_i32(&a.ls->exiting) != 0) break;  // the launch is winding down
           const unsigned long long tail = ld_acquire_sys_u64(&a.ring->tail);
           const unsigned int h = ld_volatile_i32(reinterpret_cast<const int*>(&a.ls->queue_head));
           if (h < tail) {
             if (atomicCAS(&a.ls->queue_head, h, h + 1u) == h) {
               got = h;
+              atomicAdd(&a.ls->busy, 1);
               break;
             }
             continue;
           }
-          if (globaltimer_ns() - t0 > a.idle_ns) break;
+          // leave only when the whole launch has been idle for idle_ns (no job
+          // running, none finished recently): a team that left cannot come
+          // back before the next launch
+          const unsigned long long now = globaltimer_ns();
+          if (now - t0 > a.idle_ns && ld_volatile_i32(&a.ls->busy) == 0 &&
+              now - *reinterpret_cast<volatile unsigned long long*>(&a.ls->last_ns) > a.idle_ns) {
+            atomicExch(&a.ls->exiting, 1);
+            break;
+          }
           __nanosleep(256);
         }
         a.ls->team_job[team] = static_cast<int>(got);
@@ -1017,6 +1027,9 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
       if (tm.rank == 0 && threadIdx.x == 0) {
         __threadfence_system();
         st_release_sys_i32(&a.ring->slots[j % kRingSize].done, 1);
+        atomicExch(&a.ls->last_ns, globaltimer_ns());
+        __threadfence();
+        atomicSub(&a.ls->busy, 1);
       }
     }
     team_exit(tm);
@@ -2087,6 +2100,8 @@ fct_status server_ensure_running(fct_server S) {
     FCT_CUDA(cudaMemcpy(&err, &S->ls->err, sizeof(int), cudaMemcpyDeviceToHost));
     if (err != 0) return fail(static_cast<fct_status>(err), "serving launch ended with a device-side error");
   }
+  // busy, exiting and last_ns start from zero; queue_head keeps its place in the ring
+  FCT_CUDA(cudaMemsetAsync(&S->ls->busy, 0, 2 * sizeof(int) + sizeof(unsigned long long), S->stream));
   SolveArgs a{};
   a.jobs = nullptr;
   a.njobs = 0;

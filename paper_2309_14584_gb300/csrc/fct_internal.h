@@ -117,14 +117,24 @@ struct TeamBarrier {
   unsigned int pad1[31];
 };
 
-// Per-launch device state (zeroed before every launch).
+// Per-launch device state (zeroed before every launch; a serving launch keeps
+// queue_head and resets busy / exiting / last_ns).
 struct LaunchState {
   unsigned int queue_head;
   int err;
-  int pad[30];
+  // serving mode: teams stay while any job runs or ran recently, and once one
+  // team decides the whole launch is idle, no team claims another job
+  int busy;                   // jobs in progress
+  int exiting;                // set by the first team that leaves
+  unsigned long long last_ns; // %globaltimer at the last job claim or finish
+  int pad[26];
   int team_job[kMaxTeams];
   TeamBarrier bars[kMaxTeams];
 };
+static_assert(offsetof(LaunchState, exiting) == offsetof(LaunchState, busy) + 4 &&
+                  offsetof(LaunchState, last_ns) == offsetof(LaunchState, busy) + 8 &&
+                  offsetof(LaunchState, team_job) == 128,
+              "LaunchState layout");
 
 // Serving ring in host-mapped memory: the host publishes jobs (slot then
 // tail, release), team leaders claim them through LaunchState::queue_head,

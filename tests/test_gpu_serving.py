@@ -82,3 +82,41 @@ def test_jobs_submitted_while_others_run_join_them():
     F.fct_server_destroy(srv)
     for p in ps + [pl]:
         p.close()
+
+
+def test_teams_stay_while_a_long_job_runs():
+    """The server is left idle longer than its idle timeout while one long
+    transform runs on one team; short jobs submitted afterwards still run on
+    the other teams and finish first (no team left the launch)."""
+    long_w = W.config_d10_rational()
+    short = _shapes()
+    pl = F.Plan(long_w.support, long_w.sizes, long_w.nodes, precision=F.FCT_FP64, tol=1e-13)
+    ps = [F.Plan(w.support, w.sizes, w.nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5) for w in short]
+    xl = torch.empty(pl.M, dtype=torch.float64, device="cuda")
+    pl.sample(long_w.family, long_w.params, xl)
+    xs = []
+    for p, w in zip(ps, short):
+        x = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(W.FAMILY_GAUSSCOS, W.gausscos_params(11, w.D), x)
+        xs.append(x)
+    ol = torch.empty(pl.N, dtype=torch.float64, device="cuda")
+    osh = [torch.empty(p.N, dtype=torch.float64, device="cuda") for p in ps]
+    torch.cuda.synchronize()
+    srv = F.fct_server_create(0, 8, 0, 0.01)
+    tl = F.fct_server_submit(srv, pl.handle, xl, ol)
+    time.sleep(0.05)  # five idle timeouts with only the long job on the device
+    ts = [F.fct_server_submit(srv, p.handle, x, o) for p, x, o in zip(ps, xs, osh)]
+    order = []
+    pending = {tl: "long", **{t: f"short{i}" for i, t in enumerate(ts)}}
+    t0 = time.time()
+    while pending and time.time() - t0 < 60:
+        for t in list(pending):
+            r = F.fct_server_poll(srv, t)
+            if r is not None:
+                assert r["status"] == 0
+                order.append(pending.pop(t))
+    assert not pending
+    assert order[-1] == "long", order
+    F.fct_server_destroy(srv)
+    for p in ps + [pl]:
+        p.close()
