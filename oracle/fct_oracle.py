@@ -20,8 +20,9 @@ in a given candidate order until kappa(A) <= kappa0.
 
 Readings of the paper this oracle follows (each also listed in the design doc):
   * grid: Chebyshev extrema x_j = cos(pi j / (n-1)), j = 0..n-1, with a DCT-I
-    per axis and an unsigned fold (the paper's first-kind grid / DCT-II form
-    is not part of this module);
+    per axis and an unsigned fold; the paper's own form (first-kind points,
+    1/M DCT-II quadrature, signed half-weight alias entries, Eq.
+    (aliasing_matrix_1d)) is the ``kind="first"`` variant;
   * normalisation: b holds the exact Chebyshev coefficients of the grid
     interpolant, so A has unit entries times single-point weights;
   * an axis with one point samples at a given node xi and contributes the
@@ -98,8 +99,9 @@ def extrema_nodes(n: int, xi: float = 1.0) -> np.ndarray:
     return x
 
 
-def grid_axes(sizes_l, nodes_l) -> list[np.ndarray]:
-    return [extrema_nodes(int(n), float(xi)) for n, xi in zip(sizes_l, nodes_l)]
+def grid_axes(sizes_l, nodes_l, kind: str = "extrema") -> list[np.ndarray]:
+    nodes_fn = extrema_nodes if kind == "extrema" else first_kind_nodes
+    return [nodes_fn(int(n), float(xi)) for n, xi in zip(sizes_l, nodes_l)]
 
 
 def _broadcast_axis(v: np.ndarray, i: int, D: int) -> np.ndarray:
@@ -149,9 +151,9 @@ def sample_poly_bruteforce(coeffs: np.ndarray, support: np.ndarray, axes) -> np.
     return out.reshape(shape)
 
 
-def sample_lgrid(family, params, support, sizes, nodes) -> np.ndarray:
+def sample_lgrid(family, params, support, sizes, nodes, kind: str = "extrema") -> np.ndarray:
     """Concatenated samples of all K grids (row-major per grid)."""
-    return np.concatenate([sample_grid(family, params, support, grid_axes(sizes[l], nodes[l])).ravel()
+    return np.concatenate([sample_grid(family, params, support, grid_axes(sizes[l], nodes[l], kind)).ravel()
                            for l in range(sizes.shape[0])])
 
 
@@ -241,32 +243,154 @@ def alias_matrix_grid_bruteforce(support, sizes_l, nodes_l) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
+# ==========================================================================
+# The paper's own grid: first-kind Chebyshev points, DCT-II with the 1/M
+# quadrature normalisation and the signed alias relation of Lemma
+# (lem:aliasing) / Eq. (aliasing_matrix_1d).  An axis with M points here is the
+# paper's "N + 1 points" (Eq. (chebyshev_grid)).
+# ==========================================================================
+def first_kind_nodes(M: int, xi: float = 1.0) -> np.ndarray:
+    """x_k = cos(theta_k), theta_k = (k + 1/2) pi / M, k = 0..M-1 (Eq.
+    (chebyshev_grid)); the mirror symmetry x_{M-1-k} = -x_k is enforced and the
+    middle point of an odd grid is exactly 0.  M == 1 is the single node xi
+    (the same reading of single-point axes as on the extrema grid)."""
+    if M == 1:
+        return np.array([xi], dtype=np.float64)
+    k = np.arange(M)
+    x = np.cos(np.pi * (2 * k + 1) / (2 * M))
+    half = M // 2
+    x[M - half:] = -x[:half][::-1]
+    if M % 2 == 1:
+        x[half] = 0.0
+    return x
+
+
+def dct2_matrix(M: int) -> np.ndarray:
+    """The quadrature of Eq. (quad_1D): b_n = (1/M) sum_k cos(n theta_k) f_k,
+    n, k = 0..M-1, with the cosine argument n (2k + 1) reduced modulo 4M in
+    integers before the call to cos."""
+    n = np.arange(M)
+    a = np.outer(n, 2 * n + 1) % (4 * M)
+    return np.cos(np.pi * a / (2 * M)) / M
+
+
+def dct2_grid(f: np.ndarray) -> np.ndarray:
+    """Apply dct2_matrix along every axis with M >= 2 (direct O(M^2))."""
+    y = np.asarray(f, dtype=np.float64)
+    for axis, M in enumerate(y.shape):
+        if M >= 2:
+            y = np.moveaxis(np.tensordot(dct2_matrix(M), y, axes=([1], [axis])), 0, axis)
+    return y
+
+
+def aliasing_delta(ell, M: int):
+    """Delta_N of Eq. (aliasing_delta) for an M = N + 1 point grid."""
+    r = np.asarray(ell, dtype=np.int64) % (4 * M)
+    return np.where(r == 0, 1.0, np.where(r == 2 * M, -1.0, 0.0))
+
+
+def aliasing_entry(n, m, M: int):
+    """A_{n,m} = Delta(m + n)/2 + Delta(m - n)/2, Eq. (aliasing_matrix_1d)."""
+    n = np.asarray(n, dtype=np.int64)
+    m = np.asarray(m, dtype=np.int64)
+    return 0.5 * aliasing_delta(m + n, M) + 0.5 * aliasing_delta(m - n, M)
+
+
+def fold_first_kind(m, M: int):
+    """Row and value of the one entry of column m in the M x inf matrix of Eq.
+    (aliasing_matrix_1d), M >= 2.  With q = m div 2M and r = m mod 2M:
+      r < M : row r,      value (-1)^q (1 if r == 0 else 1/2)
+      r > M : row 2M - r, value -(-1)^q / 2
+      r = M : no entry (T_m vanishes on every node); given row 0, value 0."""
+    m = np.asarray(m, dtype=np.int64)
+    q, r = np.divmod(m, 2 * M)
+    sgn = np.where(q % 2 == 0, 1.0, -1.0)
+    row = np.where(r < M, r, np.where(r > M, 2 * M - r, 0))
+    val = np.where(r < M, sgn * np.where(r == 0, 1.0, 0.5), np.where(r > M, -0.5 * sgn, 0.0))
+    return row, val
+
+
+def grid_bins_first_kind(support: np.ndarray, sizes_l) -> np.ndarray:
+    D = len(sizes_l)
+    strides = np.ones(D, dtype=np.int64)
+    for i in range(D - 2, -1, -1):
+        strides[i] = strides[i + 1] * int(sizes_l[i + 1])
+    sup = support.astype(np.int64)
+    bins = np.zeros(sup.shape[0], dtype=np.int64)
+    for i in range(D):
+        M = int(sizes_l[i])
+        if M >= 2:
+            bins += fold_first_kind(sup[:, i], M)[0] * strides[i]
+    return bins
+
+
+def grid_weights_first_kind(support: np.ndarray, sizes_l, nodes_l) -> np.ndarray:
+    """Entry of column m: product over axes of the 1D entries (Eq.
+    (aliasing_matrix_nd_diff) on a tensor grid) times T_{m_i}(xi_i) on
+    single-point axes."""
+    w = np.ones(support.shape[0])
+    for i, M in enumerate(sizes_l):
+        mi = support[:, i].astype(np.int64)
+        if int(M) == 1:
+            w *= chebyshev_T(mi, nodes_l[i])
+        else:
+            w *= fold_first_kind(mi, int(M))[1]
+    return w
+
+
+def alias_matrix_grid_first_kind_bruteforce(support, sizes_l, nodes_l) -> np.ndarray:
+    """Column m = the quadrature (dct2_grid) of T_m sampled on the grid; no
+    fold formula.  Tiny grids only."""
+    axes = grid_axes(sizes_l, nodes_l, "first")
+    D = len(axes)
+    cols = []
+    for m in support.astype(np.int64):
+        f = np.ones(tuple(a.size for a in axes))
+        for i in range(D):
+            f = f * _broadcast_axis(chebyshev_T(m[i], axes[i]), i, D)
+        cols.append(dct2_grid(f).ravel())
+    return np.stack(cols, axis=1)
+
+
 class AliasSystem:
     """The stacked least-squares system of Eq. (main_linear_system), rows of
-    empty bins dropped (they do not involve c)."""
+    empty bins dropped (they do not involve c).  kind = "extrema" (DCT-I on
+    extrema points, interpolation normalisation) or "first" (the paper's
+    first-kind points, 1/M quadrature and signed half-weight entries)."""
 
-    def __init__(self, support, sizes, nodes):
+    def __init__(self, support, sizes, nodes, kind: str = "extrema"):
+        if kind not in ("extrema", "first"):
+            raise ValueError(kind)
+        self.kind = kind
         self.support = np.asarray(support)
         self.sizes = np.asarray(sizes)
         self.nodes = np.asarray(nodes)
         K = self.sizes.shape[0]
+        N = self.support.shape[0]
         self.T = np.prod(self.sizes.astype(np.int64), axis=1)
         self.offsets = np.concatenate([[0], np.cumsum(self.T)])
         blocks, self.rows = [], []
         for l in range(K):
-            Al = alias_matrix_grid(self.support, self.sizes[l], self.nodes[l])
-            nonempty = np.unique(grid_bins(self.support, self.sizes[l]))
+            if kind == "extrema":
+                bins = grid_bins(self.support, self.sizes[l])
+                Al = alias_matrix_grid(self.support, self.sizes[l], self.nodes[l])
+            else:
+                bins = grid_bins_first_kind(self.support, self.sizes[l])
+                Al = sp.csr_matrix((grid_weights_first_kind(self.support, self.sizes[l], self.nodes[l]),
+                                    (bins, np.arange(N))), shape=(int(self.T[l]), N))
+            nonempty = np.unique(bins)
             self.rows.append(nonempty)
             blocks.append(Al[nonempty])
         self.A = sp.vstack(blocks).tocsr()
         self.R = self.A.shape[0]
 
     def rhs(self, samples: np.ndarray) -> np.ndarray:
-        """b: per grid DCT-I of its samples, restricted to nonempty bins."""
+        """b: per grid DCT of its samples, restricted to nonempty bins."""
+        transform = dct1_grid if self.kind == "extrema" else dct2_grid
         out = []
         for l in range(self.sizes.shape[0]):
             f = samples[self.offsets[l]:self.offsets[l + 1]].reshape(tuple(int(n) for n in self.sizes[l]))
-            out.append(dct1_grid(f).ravel()[self.rows[l]])
+            out.append(transform(f).ravel()[self.rows[l]])
         return np.concatenate(out)
 
 
@@ -378,9 +502,9 @@ def solve(system: AliasSystem, b: np.ndarray, method: str = "auto", tol: float =
     raise ValueError(method)
 
 
-def fct(support, sizes, nodes, samples, method: str = "auto", tol: float = 1e-15):
+def fct(support, sizes, nodes, samples, method: str = "auto", tol: float = 1e-15, kind: str = "extrema"):
     """Algorithm 3 end to end on given samples: build A, DCT, solve."""
-    system = AliasSystem(support, sizes, nodes)
+    system = AliasSystem(support, sizes, nodes, kind)
     b = system.rhs(samples)
     return solve(system, b, method=method, tol=tol)
 

@@ -102,6 +102,25 @@ def _construct_one_late(support, cand_sizes, cand_nodes, kappa0=1e4):
     return L + 1, _orig_cond(O.AliasSystem(support, cand_sizes[:L + 1], cand_nodes[:L + 1]).A)
 
 
+_orig_fold1 = O.fold_first_kind
+
+
+def _fold1_unsigned(m, M):
+    row, val = _orig_fold1(m, M)
+    return row, np.abs(val)
+
+
+def _fold1_full_weight(m, M):
+    row, val = _orig_fold1(m, M)
+    return row, np.sign(val)
+
+
+def _fold1_no_zero_column(m, M):
+    row, val = _orig_fold1(m, M)
+    r = np.asarray(m, dtype=np.int64) % (2 * M)
+    return np.where(r == M, M - 1, row), np.where(r == M, 0.5, val)
+
+
 MUTATIONS = [
     ("fold_off_by_one", "fold", _fold_off_by_one, lambda: P.test_fold_identity_exhaustive()),
     ("fold_off_by_one_recovery", "fold", _fold_off_by_one,
@@ -119,6 +138,12 @@ MUTATIONS = [
     ("condition_squared", "condition_number", _cond_squared, lambda: P.test_condition_number_closed_forms()),
     ("alg2_one_late", "construct_alias_system", _construct_one_late,
      lambda: P.test_alg2_returns_the_first_prefix_within_bound(6.0)),
+    ("fold1_unsigned", "fold_first_kind", _fold1_unsigned,
+     lambda: P.test_first_kind_alias_matrix_equals_bruteforce(*P.TINY_FIRST[1])),
+    ("fold1_full_weight", "fold_first_kind", _fold1_full_weight,
+     lambda: P.test_first_kind_exact_recovery(62, 2, 9, 5, 2, 8)),
+    ("fold1_no_zero_column", "fold_first_kind", _fold1_no_zero_column,
+     lambda: P.test_first_kind_fold_equals_lemma_and_quadrature_exhaustive()),
 ]
 
 

@@ -377,3 +377,109 @@ def test_alg2_returns_the_first_prefix_within_bound(kappa0):
     assert _kappa_eig(_stacked_bruteforce(sup, sizes[:L], nodes[:L])) <= kappa0 * (1 + 1e-9)
     if L > 1:
         assert _kappa_eig(_stacked_bruteforce(sup, sizes[:L - 1], nodes[:L - 1])) > kappa0 * (1 - 1e-9)
+
+
+# ---------------------------------------------------------------- first-kind grid (the paper's own form)
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 7, 16, 33])
+def test_first_kind_nodes_are_roots_of_T_M(M):
+    x = O.first_kind_nodes(M, xi=0.3)
+    if M == 1:
+        assert x.tolist() == [0.3]
+        return
+    assert np.allclose(x, np.cos((np.arange(M) + 0.5) * np.pi / M), atol=2e-16)
+    assert np.all(x[::-1] == -x)
+    assert np.all(np.diff(x) < 0)
+    assert np.max(np.abs(npcheb.chebval(x, [0] * M + [1]))) < 1e-13
+
+
+def test_dct2_closed_forms():
+    """From the quadrature b_n = (1/M) sum_k cos(n theta_k) f_k, by hand:
+    M=2 (x = +-1/sqrt2): b0 = (f0+f1)/2, b1 = (f0-f1)/(2 sqrt2);
+    M=3 (x = sqrt3/2, 0, -sqrt3/2): b0 = (f0+f1+f2)/3, b1 = (f0-f2)/(2 sqrt3),
+    b2 = (f0/2 - f1 + f2/2)/3."""
+    f2 = np.array([0.7, -1.3])
+    assert np.allclose(O.dct2_matrix(2) @ f2, [(f2[0] + f2[1]) / 2, (f2[0] - f2[1]) / (2 * math.sqrt(2))],
+                       atol=1e-16)
+    f3 = np.array([0.4, 2.0, -0.9])
+    want = [f3.sum() / 3, (f3[0] - f3[2]) / (2 * math.sqrt(3)), (f3[0] / 2 - f3[1] + f3[2] / 2) / 3]
+    assert np.allclose(O.dct2_matrix(3) @ f3, want, atol=1e-16)
+    assert O.dct2_matrix(1).tolist() == [[1.0]]
+
+
+@pytest.mark.parametrize("M", [2, 5, 8, 31, 100])
+def test_dct2_matches_scipy_type2(M):
+    f = W.stream(M, "probe").standard_normal(M)
+    assert np.allclose(O.dct2_matrix(M) @ f, scipy.fft.dct(f, type=2) / (2 * M), atol=1e-14)
+
+
+@pytest.mark.parametrize("M", [2, 3, 6, 13])
+def test_dct2_of_sampled_T_is_half_unit_vector(M):
+    """Below M the quadrature is exact: T_0 -> e_0, T_n -> e_n / 2 (orthogonality)."""
+    x = O.first_kind_nodes(M)
+    for n in range(M):
+        b = O.dct2_matrix(M) @ O.chebyshev_T(n, x)
+        e = np.zeros(M)
+        e[n] = 1.0 if n == 0 else 0.5
+        assert np.allclose(b, e, atol=1e-14)
+
+
+def test_first_kind_fold_equals_lemma_and_quadrature_exhaustive():
+    """Lemma (lem:aliasing): the quadrature of cos(n theta) cos(m theta) over
+    the M first-kind points equals Delta(m+n)/2 + Delta(m-n)/2 (computed from
+    Eq. (aliasing_delta)); the signed fold gives exactly those entries."""
+    for M in range(2, 41):
+        th = (np.arange(M) + 0.5) * np.pi / M
+        n = np.arange(M)
+        m = np.arange(20 * M)
+        quad = np.cos(np.outer(n, th)) @ np.cos(np.outer(th, m)) / M          # [M, 20M]
+        lem = O.aliasing_entry(n[:, None], m[None, :], M)
+        assert np.max(np.abs(quad - lem)) < 1e-12
+        row, val = O.fold_first_kind(m, M)
+        dense = np.zeros((M, m.size))
+        dense[row, m] = val
+        assert np.array_equal(dense, lem)
+
+
+TINY_FIRST = [
+    (1, 9, [[4], [7]], [[0.0], [0.0]]),
+    (2, 5, [[3, 4], [1, 6], [5, 1]], [[0.0, 0.0], [0.41, 0.0], [0.0, -0.77]]),
+    (3, 3, [[2, 3, 2], [4, 1, 3]], [[0.0, 0.0, 0.0], [0.0, 0.25, 0.0]]),
+]
+
+
+@pytest.mark.parametrize("D,d,sizes,nodes", TINY_FIRST)
+def test_first_kind_alias_matrix_equals_bruteforce(D, d, sizes, nodes):
+    sup = W.total_degree_support(D, d)
+    for l in range(len(sizes)):
+        bins = O.grid_bins_first_kind(sup, sizes[l])
+        w = O.grid_weights_first_kind(sup, sizes[l], nodes[l])
+        T = int(np.prod(sizes[l]))
+        dense = np.zeros((T, sup.shape[0]))
+        dense[bins, np.arange(sup.shape[0])] = w
+        brute = O.alias_matrix_grid_first_kind_bruteforce(sup, sizes[l], nodes[l])
+        assert np.max(np.abs(dense - brute)) < 1e-13
+
+
+@pytest.mark.parametrize("seed,D,d,K,lo,hi", [(61, 1, 14, 6, 4, 11), (62, 2, 9, 5, 2, 8), (63, 3, 5, 9, 1, 6),
+                                              (64, 4, 4, 12, 1, 5)])
+def test_first_kind_exact_recovery(seed, D, d, K, lo, hi):
+    w = W.make_workload("fk", seed, D, d, K, lo, hi, W.FAMILY_POLY)
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes, kind="first")
+    c = O.fct(w.support, w.sizes, w.nodes, f, "qr", kind="first")
+    assert np.linalg.norm(c - w.coeffs_true) <= 1e-12 * np.linalg.norm(w.coeffs_true)
+
+
+def test_first_kind_full_grid_is_scaled_selection():
+    """One grid with M_i >= d + 1 points per axis: no collision; the entry of
+    m is prod_i (1 if m_i = 0 else 1/2), and c* = b / entry."""
+    D, d = 3, 4
+    sup = W.total_degree_support(D, d)
+    sizes = np.array([[d + 1, d + 2, d + 1]], dtype=np.int32)
+    s = O.AliasSystem(sup, sizes, np.zeros((1, D)), kind="first")
+    assert s.R == sup.shape[0]
+    want = np.prod(np.where(sup == 0, 1.0, 0.5), axis=1)
+    assert np.allclose(np.abs(s.A).sum(axis=0).A1, want, atol=0)
+    f = O.sample_lgrid(W.FAMILY_RATIONAL, W.rational_params(3, D), sup, sizes, np.zeros((1, D)), kind="first")
+    c = O.solve(s, s.rhs(f), "qr")
+    y = O.dct2_grid(f.reshape(tuple(sizes[0])))[tuple(sup.T.astype(np.int64))]
+    assert np.max(np.abs(c - y / want)) < 1e-14
