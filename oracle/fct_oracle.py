@@ -522,6 +522,23 @@ def condition_number(A) -> float:
     return float(sv[0] / sv[-1])
 
 
+def evaluate_expansion(coeffs, support, points) -> np.ndarray:
+    """p(x) = sum_m c_m prod_i T_{m_i}(x_i) (Eq. (chebyshev_expansion)) at each
+    row of points [P, D], term by term with T from its definition
+    cos(m arccos x).  The paper measures approximation error this way, at
+    random points (Sec. 4)."""
+    pts = np.atleast_2d(np.asarray(points, dtype=np.float64))
+    sup = np.asarray(support).astype(np.int64)
+    c = np.asarray(coeffs, dtype=np.float64)
+    out = np.empty(pts.shape[0])
+    for p in range(pts.shape[0]):
+        terms = np.ones(sup.shape[0])
+        for i in range(sup.shape[1]):
+            terms *= chebyshev_T(sup[:, i], pts[p, i])
+        out[p] = terms @ c
+    return out
+
+
 def construct_alias_system(support, cand_sizes, cand_nodes, kappa0: float = 1e4):
     """Algorithm 2 (Sec. 3.3): starting from no grids, append the next grid of
     the candidate sequence (each one an Algorithm 1 draw, passed in) until the

@@ -121,6 +121,13 @@ def _fold1_no_zero_column(m, M):
     return np.where(r == M, M - 1, row), np.where(r == M, 0.5, val)
 
 
+_orig_eval = O.evaluate_expansion
+
+
+def _eval_axes_swapped(coeffs, support, points):
+    return _orig_eval(coeffs, support, np.atleast_2d(points)[:, ::-1])
+
+
 MUTATIONS = [
     ("fold_off_by_one", "fold", _fold_off_by_one, lambda: P.test_fold_identity_exhaustive()),
     ("fold_off_by_one_recovery", "fold", _fold_off_by_one,
@@ -144,6 +151,8 @@ MUTATIONS = [
      lambda: P.test_first_kind_exact_recovery(62, 2, 9, 5, 2, 8)),
     ("fold1_no_zero_column", "fold_first_kind", _fold1_no_zero_column,
      lambda: P.test_first_kind_fold_equals_lemma_and_quadrature_exhaustive()),
+    ("eval_axes_swapped", "evaluate_expansion", _eval_axes_swapped,
+     lambda: P.test_evaluate_matches_numpy_chebval_1d_and_2d()),
 ]
 
 

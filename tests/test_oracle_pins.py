@@ -483,3 +483,28 @@ def test_first_kind_full_grid_is_scaled_selection():
     c = O.solve(s, s.rhs(f), "qr")
     y = O.dct2_grid(f.reshape(tuple(sizes[0])))[tuple(sup.T.astype(np.int64))]
     assert np.max(np.abs(c - y / want)) < 1e-14
+
+
+# ---------------------------------------------------------------- evaluation of the expansion
+def test_evaluate_matches_numpy_chebval_1d_and_2d():
+    g = W.stream(71, "probe")
+    c1 = g.standard_normal(13)
+    x = g.uniform(-1, 1, 50)
+    sup1 = np.arange(13, dtype=np.uint16).reshape(-1, 1)
+    assert np.allclose(O.evaluate_expansion(c1, sup1, x[:, None]), npcheb.chebval(x, c1), atol=1e-13)
+    sup2 = W.total_degree_support(2, 8)
+    c2 = g.standard_normal(sup2.shape[0])
+    dense = np.zeros((9, 9))
+    dense[sup2[:, 0], sup2[:, 1]] = c2
+    pts = g.uniform(-1, 1, (40, 2))
+    want = npcheb.chebval2d(pts[:, 0], pts[:, 1], dense)
+    assert np.allclose(O.evaluate_expansion(c2, sup2, pts), want, atol=1e-13)
+
+
+def test_evaluate_at_grid_points_equals_recurrence_sampler():
+    w = W.make_workload("ev", 72, 3, 5, 2, 2, 5, W.FAMILY_POLY)
+    axes = O.grid_axes(w.sizes[0], w.nodes[0])
+    pts = np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, 3)
+    got = O.evaluate_expansion(w.coeffs_true, w.support, pts)
+    want = O.sample_poly_bruteforce(w.coeffs_true, w.support, axes).ravel()
+    assert np.allclose(got, want, atol=1e-13)
