@@ -70,6 +70,9 @@ enum {
 
 typedef struct fct_plan_s* fct_plan;
 
+#define FCT_GRID_EXTREMA 0
+#define FCT_GRID_FIRST_KIND 1
+
 typedef struct {
   int precision;      /* FCT_FP64: FP64 CG on the normal equations.  FCT_MIXED: FP32
                          inner solves between FP64 residual sweeps; if a sweep gains
@@ -83,6 +86,18 @@ typedef struct {
   int max_blocks;     /* 0 = all co-resident blocks; else cap on the solver's grid      */
   int coef_lanes;     /* 0 = auto; else 1, 2, 4, 8 or 16 threads per coefficient in A^T r */
   double timeout_s;   /* bound on any device-side wait (default 4 s)                    */
+  int normal_matrix;  /* FCT_MIXED inner solve: 0 = auto, 1 = on, -1 = off.  On: the plan
+                         stores W = A^T A (CSR, FP32) and the inner solve is CG on
+                         W d = g in pipelined form (one team barrier per iteration
+                         instead of two); auto turns it on when W has no more
+                         nonzeros than A and A^T together (2 K N) and at most 8 M.   */
+  int grid_kind;      /* FCT_GRID_EXTREMA (default): n extrema points cos(pi j/(n-1)),
+                         interpolating DCT-I, unit alias entries.  FCT_GRID_FIRST_KIND:
+                         the paper's own form, Eq. (chebyshev_grid) with n points
+                         cos((j+1/2) pi/n), the 1/n DCT-II quadrature of Eq. (quad_1D)
+                         and the signed entries 1, +-1/2, 0 of Eq. (aliasing_matrix_1d)
+                         (Lemma lem:aliasing), multiplied over axes.  Single-point
+                         axes sample the given node in both kinds.                  */
 } fct_options;
 
 typedef struct {
@@ -105,10 +120,11 @@ typedef struct {
   int32_t block_threads;
   int32_t coef_lanes;
   int64_t device_bytes;     /* tables + workspace held on the device               */
+  int64_t normal_nnz;       /* nonzeros of W = A^T A when the plan stores it, else 0 */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,
- * max_refine 6, automatic launch shape, 4 s wait bound. */
+ * max_refine 6, automatic launch shape, 4 s wait bound, normal matrix auto. */
 void fct_default_options(fct_options* opt);
 
 /* Thread-local message of the last failing call (never NULL). */
@@ -275,6 +291,19 @@ fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* 
 fct_status fct_plan_condition(fct_plan plan, const double* start, double* work, int iterations,
                               double* kappa, double* lambda_min, double* lambda_max, int* used, void* stream);
 
+/*
+ * Evaluate the expansion p(x) = sum_m coeffs[m] prod_i T_{m_i}(x_i)
+ * (Eq. (chebyshev_expansion)) over the plan's support at npoints points, the
+ * way the paper measures approximation error (at random points, Sec. 4).
+ *   coeffs: device double[N], support order (fct_execute's output);
+ *   points: device double[npoints][D], row-major, normally in [-1, 1]^D;
+ *   values: device double[npoints].
+ * T_k comes from the three-term recurrence up to the support's largest
+ * degree.  npoints = 0 is a no-op.  Asynchronous on stream.
+ */
+fct_status fct_evaluate(fct_plan plan, const double* coeffs, int64_t npoints, const double* points, double* values,
+                        void* stream);
+
 /* Release a plan's device memory (synchronises the device first). NULL is OK. */
 fct_status fct_destroy(fct_plan plan);
 
@@ -284,11 +313,15 @@ fct_status fct_destroy(fct_plan plan);
  *         its one nonzero within grid l's full DCT output);
  *   crow  host int32[K][N]: global compressed row of that nonzero, rows
  *         numbered grid by grid, nonempty bins in ascending bin order;
- *   weight host double[K][N]: the entry, prod over n_i == 1 of T_{m_i}(xi_i);
- *   *R_out: number of nonempty rows.  Any output pointer may be NULL.
+ *   weight host double[K][N]: the entry, prod over n_i == 1 of T_{m_i}(xi_i)
+ *         (first-kind grid: times the signed 1D entries of active axes; a
+ *         degree with no entry on a grid gets bin index 0 on that axis and
+ *         weight 0);
+ *   *R_out: number of nonempty rows.  grid_kind: FCT_GRID_EXTREMA or
+ *   FCT_GRID_FIRST_KIND (see fct_options).  Any output pointer may be NULL.
  */
 fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,
-                                 const int32_t* sizes, const double* nodes, int32_t* bin,
+                                 const int32_t* sizes, const double* nodes, int grid_kind, int32_t* bin,
                                  int32_t* crow, double* weight, int64_t* R_out);
 
 #ifdef __cplusplus

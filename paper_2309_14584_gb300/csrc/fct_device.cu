@@ -75,6 +75,25 @@ struct Team {
   unsigned long long timeout_ns;
 };
 
+// Wait (thread 0) until the team counter reaches target, polling with
+// gpu-scope acquire loads (measured faster than relaxed polls closed by an
+// acq_rel fence).  The error flag and the time limit are checked every 16
+// polls, which keeps the poll loop to one load.  Returns 0 when the launch is
+// being abandoned (a wait expired here or elsewhere).
+__device__ __forceinline__ int bar_wait(const Team& tm, unsigned int target) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (unsigned int spin = 1;; ++spin) {
+    if (ld_acquire_u32(&tm.bar->count) >= target) return 1;
+    if ((spin & 15u) == 0) {
+      if (ld_volatile_i32(tm.err) != 0) return 0;
+      if (globaltimer_ns() - t0 > tm.timeout_ns) {
+        atomicCAS(tm.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
+        return 0;
+      }
+    }
+  }
+}
+
 // Team-wide barrier: arrive with a release increment of the team's monotonic
 // counter, wait (bounded) until it reaches G x barrier number.  Returns false
 // when the launch is being abandoned (a wait expired here or elsewhere).
@@ -87,20 +106,7 @@ __device__ bool team_sync(Team& tm) {
     if (tm.G > 1) {
       const unsigned int target = tm.epoch * static_cast<unsigned int>(tm.G);
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&tm.bar->count) : "memory");
-      if (ld_acquire_u32(&tm.bar->count) < target) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (ld_acquire_u32(&tm.bar->count) < target) {
-          if (ld_volatile_i32(tm.err) != 0) {
-            ok = 0;
-            break;
-          }
-          if (globaltimer_ns() - t0 > tm.timeout_ns) {
-            atomicCAS(tm.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
-            ok = 0;
-            break;
-          }
-        }
-      }
+      ok = bar_wait(tm, target);
     } else {
       __threadfence();
       if (ld_volatile_i32(tm.err) != 0) ok = 0;
@@ -131,16 +137,21 @@ __device__ void team_exit(const Team& tm) {
 // the last nk units (wpart); warp 0 stores the unit partials part[u0 + i*G]
 // and its lane 0 arrives at and waits on the team barrier, so one block-wide
 // sync before and one after cover both the flush and the barrier.
-template <int NW>
-__device__ bool phase_end(Team& tm, const float (*wpart)[NW], float* part, int u0, int nk) {
+__device__ __forceinline__ float padd(float a, float b) { return a + b; }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float pzero(float) { return 0.0f; }
+__device__ __forceinline__ float2 pzero(float2) { return make_float2(0.0f, 0.0f); }
+
+template <int NW, typename PT>
+__device__ bool phase_end(Team& tm, const PT (*wpart)[NW], PT* part, int u0, int nk) {
   __shared__ int s_ok2;
   __syncthreads();
   tm.epoch += 1;
   if (threadIdx.x < 32) {
     if (static_cast<int>(threadIdx.x) < nk) {
-      float v = 0.0f;
+      PT v = pzero(PT{});
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v += wpart[threadIdx.x][w];
+      for (int w = 0; w < NW; ++w) v = padd(v, wpart[threadIdx.x][w]);
       stcg(part + u0 + static_cast<int>(threadIdx.x) * tm.G, v);
     }
     __syncwarp();
@@ -149,20 +160,7 @@ __device__ bool phase_end(Team& tm, const float (*wpart)[NW], float* part, int u
       if (tm.G > 1) {
         const unsigned int target = tm.epoch * static_cast<unsigned int>(tm.G);
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&tm.bar->count) : "memory");
-        if (ld_acquire_u32(&tm.bar->count) < target) {
-          const unsigned long long t0 = globaltimer_ns();
-          while (ld_acquire_u32(&tm.bar->count) < target) {
-            if (ld_volatile_i32(tm.err) != 0) {
-              ok = 0;
-              break;
-            }
-            if (globaltimer_ns() - t0 > tm.timeout_ns) {
-              atomicCAS(tm.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
-              ok = 0;
-              break;
-            }
-          }
-        }
+        ok = bar_wait(tm, target);
       } else {
         __threadfence();
         if (ld_volatile_i32(tm.err) != 0) ok = 0;
@@ -210,16 +208,35 @@ __device__ __forceinline__ void warp0_team_sum(const double* part, int n, double
 
 // Warp 0: FP32 sum of n chunk partials in a fixed order, left in *out (lane 0).
 __device__ __forceinline__ float warp0_team_sum_f(const float* part, int n) {
+  // 16 independent loads per lane per round: up to 512 partials in one L2 round trip
   float v = 0.0f;
-  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
-    float t[8];
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 16) {
+    float t[16];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0f;
+    for (int j = 0; j < 16; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) v += t[j];
+    for (int j = 0; j < 16; ++j) v += t[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Warp 0: FP32 pair sums of n partials in a fixed order (lane 0 holds the result).
+__device__ __forceinline__ float2 warp0_team_sum_f2(const float2* part, int n) {
+  float2 v = make_float2(0.0f, 0.0f);
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 4) {
+    float2 t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v = padd(v, t[j]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
   return v;
 }
 
@@ -260,16 +277,22 @@ __device__ __forceinline__ V lane_group_sum(V v, int L) {
 struct BlockTabs {
   const int* hdrA;      // [nA][5]
   const int* hdrB;      // [nB]
+  const int* hdrW;      // [nW][2] {entries, pool offset}
   const int* pool;
-  int cachedA, cachedB;
+  int cachedA, cachedB, cachedW;
   const double* mats;   // DCT matrices (shared copy or global)
 };
 
+//   W units (rows of A^T A, mixed path only; staged first, since the inner
+//   solve runs most often): pool holds rowptr[m0..m1] - jbase, the columns,
+//   then the FP32 values (as bits).
 template <int BT>
-__device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char* dsm, int smem_bytes, BlockTabs* T) {
-  const int nru = P.n_row_units, ncc = P.n_coef_chunks;
+__device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char* dsm, int smem_bytes, BlockTabs* T,
+                                bool with_w) {
+  const int nru = P.n_row_units, ncc = P.n_coef_chunks, nwu = with_w ? P.n_w_units : 0;
   const int nA = nru > tm.rank ? (nru - tm.rank + tm.G - 1) / tm.G : 0;
   const int nB = ncc > tm.rank ? (ncc - tm.rank + tm.G - 1) / tm.G : 0;
+  const int nW = nwu > tm.rank ? (nwu - tm.rank + tm.G - 1) / tm.G : 0;
   int off = 0;
   const double* mats = P.dct_mats;
   if (P.mats_smem > 0 && static_cast<int>(P.mats_smem * sizeof(double)) <= smem_bytes) {
@@ -280,10 +303,31 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   }
   int* hdrA = reinterpret_cast<int*>(dsm + off);
   int* hdrB = hdrA + 5 * nA;
-  int* pool = hdrB + nB;
-  const int cap = (smem_bytes - off) / 4 - 5 * nA - nB;  // ints left for the pool
-  int used = 0, cachedA = 0, cachedB = 0;
+  int* hdrW = hdrB + nB;
+  int* pool = hdrW + 2 * nW;
+  const int cap = (smem_bytes - off) / 4 - 5 * nA - nB - 2 * nW;  // ints left for the pool
+  int used = 0, cachedA = 0, cachedB = 0, cachedW = 0;
   if (cap > 0) {
+    for (int k = 0; k < nW; ++k) {
+      const int u = tm.rank + k * tm.G;
+      const int m0 = u * P.w_rows_per_unit, m1 = min(P.N, m0 + P.w_rows_per_unit);
+      const int jbase = __ldg(P.wrowptr + m0), e = __ldg(P.wrowptr + m1) - jbase;
+      const int need = (m1 - m0 + 1) + 2 * e;
+      if (used + need > cap) break;
+      int* rp = pool + used;
+      for (int i = threadIdx.x; i <= m1 - m0; i += BT) rp[i] = __ldg(P.wrowptr + m0 + i) - jbase;
+      int* cl = rp + (m1 - m0 + 1);
+      for (int i = threadIdx.x; i < e; i += BT) {
+        cl[i] = __ldg(P.wcol + jbase + i);
+        cl[e + i] = __float_as_int(__ldg(P.wval + jbase + i));
+      }
+      if (threadIdx.x == 0) {
+        hdrW[2 * k] = e;
+        hdrW[2 * k + 1] = used;
+      }
+      used += need;
+      cachedW = k + 1;
+    }
     for (int k = 0; k < nA; ++k) {
       const int u = tm.rank + k * tm.G;
       const int r0 = __ldg(P.ru_first + u), r1 = __ldg(P.ru_first + u + 1);
@@ -325,9 +369,11 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   __syncthreads();
   T->hdrA = hdrA;
   T->hdrB = hdrB;
+  T->hdrW = hdrW;
   T->pool = pool;
   T->cachedA = cachedA;
   T->cachedB = cachedB;
+  T->cachedW = cachedW;
   T->mats = mats;
 }
 
@@ -770,6 +816,253 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
 }
 
 // ---------------------------------------------------------------------------
+// Inner solve of the mixed path on the stored normal matrix W = A^T A: CG on
+// W d = g in its pipelined form (Ghysels and Vanroose), whose two inner
+// products of an iteration are formed together with the vector updates, so
+// an iteration is one gather y = W w plus one team barrier (the two-matrix
+// form needs a barrier after A p and another after A^T q).
+//   vectors (FP32, owned by the thread group of their row): r, p, s = W p,
+//   z = W s, w = W r (two buffers: one is gathered while the next is written),
+//   x = dx32; right-hand side: sp32[m].x; start x = 0.
+//   per iteration, with gamma = r.r, delta = w.r from the previous barrier:
+//     beta = gamma / gamma_prev, alpha = gamma / (delta - beta gamma / alpha_prev)
+//     z = y + beta z, s = w + beta s, p = r + beta p
+//     x += alpha p, r -= alpha s, w -= alpha z
+// The w gathers use plain (L1-cached) loads: every team barrier ends with a
+// gpu-scope acquire, which invalidates L1, and w is not written while it is
+// gathered.
+// ---------------------------------------------------------------------------
+template <int BT>
+__device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, double gamma0, double tol, int max_iter,
+                             int stall, int* iters_out, double* gamma_out, int* status_out) {
+  constexpr int NW = BT / 32 - 1;
+  __shared__ float2 wpart2[kUnitGroup][NW];
+  __shared__ float sh_ab[3];   // alpha, beta, final relative gamma
+  __shared__ int sh_ctl[2];    // stop flag, iterations
+  *status_out = FCT_OK;
+  *iters_out = 0;
+  *gamma_out = gamma0;
+  if (!(gamma0 > 0.0) || !isfinite(gamma0)) {
+    if (!isfinite(gamma0)) *status_out = FCT_ERR_NONFINITE;
+    return true;
+  }
+  const int N = P.N, nwu = P.n_w_units, LW = P.w_lanes, rpw = P.w_rows_per_unit;
+  const int wk = static_cast<int>(threadIdx.x) - 32;
+  const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
+  const int lane32 = threadIdx.x & 31;
+  const float rs = static_cast<float>(1.0 / sqrt(gamma0));
+  const float tol2 = static_cast<float>(tol * tol);
+  float* const wb0 = P.wv;
+  float* const wb1 = P.wv + N;
+  float* const vr = P.wv + 2 * static_cast<size_t>(N);
+  float* const vp = P.wv + 3 * static_cast<size_t>(N);
+  float* const vs = P.wv + 4 * static_cast<size_t>(N);
+  float* const vz = P.wv + 5 * static_cast<size_t>(N);
+  float* const vx = P.dx32;
+  const float* const rhs = reinterpret_cast<const float*>(P.sp32);  // .x of {s, p}: stride 2
+  // thread 0's state
+  float gam_prev = 1.0f, al_prev = 1.0f, best = 3.0e38f, gam_last = 1.0f;
+  int best_it = 0;
+
+  // y[m] = sum_j W[m][j] src[j * stride] for row m of unit u (k-th unit of this block)
+  auto gather = [&](int u, int k, const float* src, int stride, int* m_out, bool* lead) -> float {
+    const int g = wk / LW, lane = wk & (LW - 1);
+    const int m0 = u * rpw, m = m0 + g;
+    *m_out = m;
+    *lead = lane == 0 && m < N;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    if (m < N) {
+      const int* cl;
+      const float* vl;
+      int j0, j1;
+      if (k < T.cachedW) {
+        const int e = T.hdrW[2 * k];
+        const int* rp = T.pool + T.hdrW[2 * k + 1];
+        const int nrows = min(N, m0 + rpw) - m0;
+        cl = rp + nrows + 1;
+        vl = reinterpret_cast<const float*>(cl + e);
+        j0 = rp[g];
+        j1 = rp[g + 1];
+      } else {
+        cl = P.wcol;
+        vl = P.wval;
+        j0 = __ldg(P.wrowptr + m);
+        j1 = __ldg(P.wrowptr + m + 1);
+      }
+      int j = j0 + lane;
+      for (; j + 3 * LW < j1; j += 4 * LW) {
+        const int c0 = cl[j], c1 = cl[j + LW], c2 = cl[j + 2 * LW], c3 = cl[j + 3 * LW];
+        const float v0 = vl[j], v1 = vl[j + LW], v2 = vl[j + 2 * LW], v3 = vl[j + 3 * LW];
+        a0 = fmaf(v0, src[static_cast<size_t>(c0) * stride], a0);
+        a1 = fmaf(v1, src[static_cast<size_t>(c1) * stride], a1);
+        a2 = fmaf(v2, src[static_cast<size_t>(c2) * stride], a2);
+        a3 = fmaf(v3, src[static_cast<size_t>(c3) * stride], a3);
+      }
+      for (; j < j1; j += LW) a0 = fmaf(vl[j], src[static_cast<size_t>(cl[j]) * stride], a0);
+    }
+    return lane_group_sum((a0 + a1) + (a2 + a3), LW);
+  };
+  auto warp_part2 = [&](int kk, float2 v) {
+    v.x = warp_sum(v.x);
+    v.y = warp_sum(v.y);
+    if (wk >= 0 && lane32 == 0) wpart2[kk][warp] = v;
+  };
+  auto flush2 = [&](float2* part, int u0, int nk) {
+    __syncthreads();
+    if (threadIdx.x < nk) {
+      float2 v = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int w2 = 0; w2 < NW; ++w2) v = padd(v, wpart2[threadIdx.x][w2]);
+      stcg(part + u0 + threadIdx.x * tm.G, v);
+    }
+    __syncthreads();
+  };
+
+  // ---- set-up: r = g, x = 0, w = W r; partials (r.r, w.r) into buffer 0
+  {
+    int k = 0, kg = 0, u0 = tm.rank;
+    for (int u = tm.rank; u < nwu; u += tm.G, ++k) {
+      int m = 0;
+      bool lead = false;
+      float y = 0.0f;
+      if (wk >= 0) y = gather(u, k, rhs, 2, &m, &lead);
+      float2 part = make_float2(0.0f, 0.0f);
+      if (wk >= 0 && lead) {
+        const float r = ldcg(rhs + 2 * static_cast<size_t>(m));
+        stcg(vr + m, r);
+        stcg(wb0 + m, y);
+        stcg(vx + m, 0.0f);
+        const float tr = r * rs, tw = y * rs;
+        part = make_float2(tr * tr, tw * tr);
+      }
+      warp_part2(kg, part);
+      if (++kg == kUnitGroup && u + tm.G < nwu) {
+        flush2(P.pw32, u0, kg);
+        kg = 0;
+        u0 = u + tm.G;
+      }
+    }
+    if (!phase_end<NW>(tm, wpart2, P.pw32, u0, kg)) return false;
+  }
+  int ctl = 0, it = 0;
+  for (;; ++it) {
+    const float* wcur = (it & 1) ? wb1 : wb0;
+    float* wnext = (it & 1) ? wb0 : wb1;
+    const float2* pin = P.pw32 + ((it & 1) ? nwu : 0);
+    float2* pout = P.pw32 + ((it & 1) ? 0 : nwu);
+    int u = tm.rank;
+    int m = 0;
+    bool lead = false;
+    float y = 0.0f, r = 0.0f, pv = 0.0f, sv = 0.0f, zv = 0.0f, xv = 0.0f, wv = 0.0f;
+    auto own_load = [&]() {
+      r = ldcg(vr + m);
+      wv = ldcg(wcur + m);
+      xv = ldcg(vx + m);
+      if (it > 0) {
+        pv = ldcg(vp + m);
+        sv = ldcg(vs + m);
+        zv = ldcg(vz + m);
+      }
+    };
+    if (wk >= 0) {
+      if (u < nwu) {
+        y = gather(u, 0, wcur, 1, &m, &lead);
+        if (lead) own_load();
+      }
+    } else {
+      const float2 g = warp0_team_sum_f2(pin, nwu);
+      if (threadIdx.x == 0) {
+        int c = 0;
+        float al = 0.0f, bt = 0.0f;
+        const float gam = g.x, del = g.y;
+        gam_last = gam;
+        if (!isfinite(gam) || !isfinite(del)) {
+          c = FCT_ERR_NONFINITE + 16;
+        } else if (gam <= tol2) {
+          c = 1;
+        } else if (it >= max_iter) {
+          c = FCT_ERR_NOCONV + 16;
+        } else {
+          if (stall > 0) {
+            if (gam < best) {
+              best = gam;
+              best_it = it;
+            } else if (it - best_it >= stall) {
+              c = 1;
+            }
+          }
+          if (c == 0) {
+            bt = it == 0 ? 0.0f : gam / gam_prev;
+            const float den = it == 0 ? del : del - bt * gam / al_prev;
+            if (!(den > 0.0f)) {
+              c = 1;  // W is positive semidefinite: no further progress in this precision
+            } else {
+              al = gam / den;
+              gam_prev = gam;
+              al_prev = al;
+            }
+          }
+        }
+        sh_ab[0] = al;
+        sh_ab[1] = bt;
+        sh_ctl[0] = c;
+      }
+    }
+    __syncthreads();
+    ctl = sh_ctl[0];
+    if (ctl != 0) break;
+    const float al = sh_ab[0], bt = sh_ab[1];
+    int k = 0, kg = 0, u0 = u;
+    for (; u < nwu; u += tm.G, ++k) {
+      if (k > 0 && wk >= 0) {
+        y = gather(u, k, wcur, 1, &m, &lead);
+        if (lead) own_load();
+      }
+      float2 part = make_float2(0.0f, 0.0f);
+      if (wk >= 0 && lead) {
+        if (it == 0) {
+          zv = y;
+          sv = wv;
+          pv = r;
+        } else {
+          zv = fmaf(bt, zv, y);
+          sv = fmaf(bt, sv, wv);
+          pv = fmaf(bt, pv, r);
+        }
+        xv = fmaf(al, pv, xv);
+        r = fmaf(-al, sv, r);
+        wv = fmaf(-al, zv, wv);
+        stcg(vz + m, zv);
+        stcg(vs + m, sv);
+        stcg(vp + m, pv);
+        stcg(vx + m, xv);
+        stcg(vr + m, r);
+        stcg(wnext + m, wv);
+        const float tr = r * rs, tw = wv * rs;
+        part = make_float2(tr * tr, tw * tr);
+      }
+      warp_part2(kg, part);
+      if (++kg == kUnitGroup && u + tm.G < nwu) {
+        flush2(pout, u0, kg);
+        kg = 0;
+        u0 = u + tm.G;
+      }
+    }
+    if (!phase_end<NW>(tm, wpart2, pout, u0, kg)) return false;
+  }
+  if (threadIdx.x == 0) {
+    sh_ctl[1] = it;
+    sh_ab[2] = gam_last;
+  }
+  __syncthreads();
+  *status_out = ctl >= 16 ? ctl - 16 : FCT_OK;
+  *iters_out = sh_ctl[1];
+  *gamma_out = static_cast<double>(sh_ab[2]) * gamma0;
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
 // One transform on the team (Algorithm 3): DCT-I of every grid, b at the
 // nonempty bins, then the FP64 solve, or FP64 normal-residual sweeps around
 // FP32 inner solves (mixed).
@@ -778,7 +1071,7 @@ template <int BT>
 __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned char* dsm, int smem_bytes) {
   const DevPlan& P = *J.plan;
   BlockTabs T;
-  load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T);
+  load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T, J.precision == FCT_MIXED && P.n_w_units > 0 && P.s_init == nullptr);
   const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units;
   const int wk = static_cast<int>(threadIdx.x) - 32;
   const int nce = (P.N + BT - 1) / BT;  // elementwise units over coefficients
@@ -860,9 +1153,14 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       int it_in = 0, st_in = FCT_OK;
       double g_in = 0.0;
       ++refines;
-      if (!cg_normal<BT, float, float, float>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32, g64 * ci * ci,
-                                              J.inner_tol, J.max_iter, 64, &it_in, &g_in, &st_in, red))
+      if (P.n_w_units > 0) {
+        if (!pcg_normal_w<BT>(P, tm, T, g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in, &st_in))
+          return false;
+      } else if (!cg_normal<BT, float, float, float>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32,
+                                                     g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in,
+                                                     &st_in, red)) {
         return false;
+      }
       iters += it_in;
       if (st_in == FCT_ERR_NONFINITE) {
         status = st_in;
@@ -1174,6 +1472,64 @@ __global__ void eval_pass_kernel(const DevPlan* __restrict__ Pp, const DctChunk*
 }
 
 // ---------------------------------------------------------------------------
+// Evaluation of the expansion p(x) = sum_m c_m prod_i T_{m_i}(x_i) at
+// arbitrary points (how the paper measures approximation error).  One warp
+// per point: its lanes build the point's T_k(x_i) tables (three-term
+// recurrence, k <= dmax) in shared memory; the block then streams the support
+// and coefficients through shared memory in tiles of kEvalTile terms, and each
+// warp sums its point's terms lane-strided and reduces by shuffles (a fixed
+// order).
+// ---------------------------------------------------------------------------
+constexpr int kEvalTile = 256;
+
+__global__ void eval_expansion_kernel(const uint16_t* __restrict__ support, const double* __restrict__ coeffs,
+                                      int N, int D, int dmax, const double* __restrict__ points, int64_t P,
+                                      double* __restrict__ values) {
+  extern __shared__ __align__(16) unsigned char esm[];
+  const int ppb = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tk = dmax + 1;
+  double* ctile = reinterpret_cast<double*>(esm);                              // [kEvalTile]
+  double* tab = ctile + kEvalTile + static_cast<size_t>(warp) * D * tk;        // [D][dmax+1] of this warp
+  uint16_t* stile = reinterpret_cast<uint16_t*>(ctile + kEvalTile + static_cast<size_t>(ppb) * D * tk);
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * ppb + warp;
+  if (p < P) {
+    for (int i = lane; i < D; i += 32) {
+      const double x = points[p * D + i];
+      double* t = tab + static_cast<size_t>(i) * tk;
+      double t0 = 1.0, t1 = x;
+      t[0] = 1.0;
+      if (dmax >= 1) t[1] = x;
+      for (int k = 2; k <= dmax; ++k) {
+        const double t2 = 2.0 * x * t1 - t0;
+        t[k] = t2;
+        t0 = t1;
+        t1 = t2;
+      }
+    }
+  }
+  double acc = 0.0;
+  for (int m0 = 0; m0 < N; m0 += kEvalTile) {
+    const int nt = min(kEvalTile, N - m0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < nt; j += blockDim.x) ctile[j] = coeffs[m0 + j];
+    for (int e = threadIdx.x; e < nt * D; e += blockDim.x) stile[e] = support[static_cast<size_t>(m0) * D + e];
+    __syncthreads();
+    if (p < P) {
+      for (int j = lane; j < nt; j += 32) {
+        double term = ctile[j];
+        const uint16_t* mj = stile + static_cast<size_t>(j) * D;
+        for (int i = 0; i < D; ++i) term *= tab[static_cast<size_t>(i) * tk + mj[i]];
+        acc += term;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (p < P && lane == 0) values[p] = acc;
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 struct fct_plan_s {
@@ -1219,6 +1575,7 @@ struct fct_plan_s {
   int smem_bytes = 0;          // dynamic shared memory requested per block
   int smem_cap = 0;            // largest request that keeps blocks_per_sm resident
   std::vector<int32_t> ru_first, rowptr_h;  // for the shared-memory sizing of other team sizes
+  std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
   bool dirty_state = false;
 };
 
@@ -1281,7 +1638,13 @@ size_t block_smem_need(const fct_plan P, int G, int rank) {
     ints += (r1 - r0 + 1) + (P->rowptr_h[r1] - P->rowptr_h[r0]);
   }
   for (int c = rank; c < hp.n_coef_chunks; c += G, ++nB) ints += static_cast<size_t>(hp.K) * hp.coefs_per_chunk;
-  ints += 5 * nA + nB;
+  int nW = 0;
+  if (hp.n_w_units > 0 && P->opt.precision == FCT_MIXED)
+    for (int u = rank; u < hp.n_w_units; u += G, ++nW) {
+      const int r0 = u * hp.w_rows_per_unit, r1 = std::min(hp.N, r0 + hp.w_rows_per_unit);
+      ints += (r1 - r0 + 1) + 2 * static_cast<size_t>(P->w_rowptr_h[r1] - P->w_rowptr_h[r0]);
+    }
+  ints += 5 * nA + nB + 2 * nW;
   return static_cast<size_t>(hp.mats_smem) * sizeof(double) + 4 * ints;
 }
 
@@ -1371,7 +1734,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   auto* P = new fct_plan_s();
   P->opt = o;
   std::string err;
-  fct_status s = build_host_tables(D, N, support, K, sizes, nodes, true, &P->H, &err);
+  fct_status s = build_host_tables(D, N, support, K, sizes, nodes, o.grid_kind, true, &P->H, &err);
   if (s != FCT_OK) {
     delete P;
     return fail(s, err);
@@ -1413,12 +1776,13 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   // one wave of co-resident blocks (a block with two units while others have
   // one makes everybody wait at the next barrier).
   int epl = 8;
+  int64_t wave = 0;  // co-resident blocks of the solver kernel
   {
     int per_sm = 0, nsm = 0, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess &&
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(BT), BT, 0) == cudaSuccess) {
-      const int64_t wave = static_cast<int64_t>(per_sm) * nsm;
+      wave = static_cast<int64_t>(per_sm) * nsm;
       for (int e : {2, 4, 8})
         if (count_row_units(H, workers, e) <= wave) {
           epl = e;
@@ -1435,6 +1799,46 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.mats_smem = H.dct_mats.size() * sizeof(double) <= 32768 ? hp.n_mats : 0;
   P->ru_first = ru_first;
   P->rowptr_h = H.rowptr;
+
+  // Normal matrix W = A^T A for the mixed path's inner solve (one team barrier
+  // per iteration instead of two).  Auto: only where W is small next to A.
+  std::vector<int32_t> w_rowptr, w_col;
+  std::vector<float> w_val32;
+  {
+    const int64_t KN2 = 2 * static_cast<int64_t>(K) * N;
+    const int64_t bound = normal_matrix_bound(H);
+    bool want = o.normal_matrix > 0 || (o.normal_matrix == 0 && o.precision == FCT_MIXED && bound <= 2 * KN2);
+    if (o.normal_matrix > 0 && bound > (int64_t{1} << 30)) {
+      delete P;
+      return fail(FCT_ERR_INVALID_ARG, "normal_matrix = 1 but A^T A would exceed 2^30 nonzeros");
+    }
+    if (want && N > 0) {
+      std::vector<double> wv64;
+      normal_matrix(H, &w_rowptr, &w_col, &wv64);
+      const int64_t nnz = static_cast<int64_t>(w_col.size());
+      if (o.normal_matrix == 0 && (nnz > KN2 || nnz > 8000000)) {
+        w_rowptr.clear();
+        w_col.clear();
+      } else {
+        w_val32.resize(nnz);
+        for (int64_t i = 0; i < nnz; ++i) w_val32[i] = static_cast<float>(wv64[i]);
+      }
+    }
+    if (!w_col.empty()) {
+      // lanes per row: as many as keep the units within one wave, at most half
+      // the mean row length
+      int LW = 32;
+      const int64_t wv = wave > 0 ? wave : 1;
+      while (LW > 1 && (N + workers / LW - 1) / (workers / LW) > wv) LW >>= 1;
+      const double mean_row = static_cast<double>(w_col.size()) / static_cast<double>(N);
+      while (LW > 1 && 2.0 * LW > mean_row) LW >>= 1;
+      hp.w_lanes = LW;
+      hp.w_rows_per_unit = workers / LW;
+      hp.n_w_units = static_cast<int32_t>((N + hp.w_rows_per_unit - 1) / hp.w_rows_per_unit);
+    }
+  }
+  const int64_t nnzw = static_cast<int64_t>(w_col.size());
+  P->w_rowptr_h = w_rowptr;
 
   // one device allocation, carved in 256-byte aligned pieces
   const int64_t KN = static_cast<int64_t>(K) * N;
@@ -1469,6 +1873,11 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&d_crow, sizeof(int32_t) * KN);
   add(&d_wcm, sizeof(double) * KN);
   add(&d_wcm32, sizeof(float) * KN);
+  int32_t *d_wrowptr, *d_wcol;
+  float* d_wval;
+  add(&d_wrowptr, sizeof(int32_t) * (nnzw > 0 ? N + 1 : 1));
+  add(&d_wcol, sizeof(int32_t) * nnzw);
+  add(&d_wval, sizeof(float) * nnzw);
   add(&hp.y0, sizeof(double) * std::max<int64_t>(H.M, 1));
   add(&hp.y1, sizeof(double) * std::max<int64_t>(H.M, 1));
   add(&hp.b, sizeof(double) * H.R);
@@ -1482,6 +1891,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&hp.q32, sizeof(float) * H.R);
   add(&hp.sp32, sizeof(float2) * N);
   add(&hp.dx32, sizeof(float) * N);
+  add(&hp.wv, sizeof(float) * (hp.n_w_units > 0 ? 6 * N : 1));
+  add(&hp.pw32, sizeof(float2) * 2 * std::max(hp.n_w_units, 1));
   add(&P->d_sizes, sizeof(int32_t) * K * D);
   add(&P->d_offsets, sizeof(int64_t) * (K + 1));
   add(&P->d_node_off, sizeof(int32_t) * K * D);
@@ -1522,6 +1933,9 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.crow = d_crow;
   hp.wcm = d_wcm;
   hp.wcm32 = d_wcm32;
+  hp.wrowptr = d_wrowptr;
+  hp.wcol = d_wcol;
+  hp.wval = d_wval;
 
   std::vector<float> w32(KN), wc32(KN);
   for (int64_t i = 0; i < KN; ++i) {
@@ -1554,6 +1968,11 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(d_crow, H.crow.data(), sizeof(int32_t) * KN));
   chk(up(d_wcm, H.weight.data(), sizeof(double) * KN));
   chk(up(d_wcm32, wc32.data(), sizeof(float) * KN));
+  if (nnzw > 0) {
+    chk(up(d_wrowptr, w_rowptr.data(), sizeof(int32_t) * (N + 1)));
+    chk(up(d_wcol, w_col.data(), sizeof(int32_t) * nnzw));
+    chk(up(d_wval, w_val32.data(), sizeof(float) * nnzw));
+  }
   chk(up(P->d_sizes, sizes, sizeof(int32_t) * K * D));
   chk(up(P->d_offsets, H.offsets.data(), sizeof(int64_t) * (K + 1)));
   chk(up(P->d_node_off, H.node_off.data(), sizeof(int32_t) * K * D));
@@ -1598,12 +2017,38 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->block_threads = P->block_threads;
   info->coef_lanes = P->hp.coef_lanes;
   info->device_bytes = static_cast<int64_t>(P->dbytes);
+  info->normal_nnz = P->hp.n_w_units > 0 ? static_cast<int64_t>(P->w_rowptr_h.back()) : 0;
   return FCT_OK;
 }
 
 fct_status fct_grid_offsets(fct_plan P, int64_t* offsets) {
   if (!P || !offsets) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
   std::memcpy(offsets, P->H.offsets.data(), sizeof(int64_t) * (P->K + 1));
+  return FCT_OK;
+}
+
+fct_status fct_evaluate(fct_plan P, const double* coeffs, int64_t npoints, const double* points, double* values,
+                        void* stream) {
+  if (!P || npoints < 0) return fail(FCT_ERR_INVALID_ARG, "NULL plan or negative point count");
+  if (npoints == 0) return FCT_OK;
+  if (!coeffs || !points || !values) return fail(FCT_ERR_INVALID_ARG, "NULL buffer");
+  const size_t per_point = sizeof(double) * static_cast<size_t>(P->D) * (P->dmax + 1);
+  const size_t fixed = sizeof(double) * kEvalTile + sizeof(uint16_t) * kEvalTile * static_cast<size_t>(P->D);
+  int dev = 0, optin = 0;
+  FCT_CUDA(cudaGetDevice(&dev));
+  FCT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  int ppb = 8;
+  while (ppb > 1 && fixed + ppb * per_point > static_cast<size_t>(optin)) ppb >>= 1;
+  const size_t smem = fixed + ppb * per_point;
+  if (smem > static_cast<size_t>(optin))
+    return fail(FCT_ERR_INVALID_ARG, "D x (max degree + 1) too large for the evaluation tables");
+  FCT_CUDA(cudaFuncSetAttribute(eval_expansion_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(smem)));
+  const int64_t blocks = (npoints + ppb - 1) / ppb;
+  if (blocks > 0x7fffffff) return fail(FCT_ERR_INVALID_ARG, "too many points");
+  eval_expansion_kernel<<<static_cast<unsigned>(blocks), 32 * ppb, smem, static_cast<cudaStream_t>(stream)>>>(
+      P->d_support, coeffs, static_cast<int>(P->N), P->D, P->dmax, points, npoints, values);
+  FCT_CUDA(cudaGetLastError());
   return FCT_OK;
 }
 
@@ -1836,6 +2281,7 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
   C->smem_cap = src->smem_cap;
   C->ru_first = src->ru_first;
   C->rowptr_h = src->rowptr_h;
+  C->w_rowptr_h = src->w_rowptr_h;
   // its own workspace, DevPlan copy, launch state and report
   DevPlan& hp = C->hp;
   const size_t M = static_cast<size_t>(std::max<int64_t>(C->M, 1)), R = static_cast<size_t>(C->R),
@@ -1861,6 +2307,8 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
       {reinterpret_cast<void**>(&hp.q32), sizeof(float) * R},
       {reinterpret_cast<void**>(&hp.sp32), sizeof(float2) * N},
       {reinterpret_cast<void**>(&hp.dx32), sizeof(float) * N},
+      {reinterpret_cast<void**>(&hp.wv), sizeof(float) * (hp.n_w_units > 0 ? 6 * N : 1)},
+      {reinterpret_cast<void**>(&hp.pw32), sizeof(float2) * 2 * std::max(hp.n_w_units, 1)},
   };
   size_t total = 0;
   for (auto& pc : pieces) total += align256(std::max<size_t>(pc.bytes, 1));
@@ -1909,7 +2357,7 @@ std::mutex g_noalloc_mu;
 
 // Layout of the workspace inside the array (256-byte aligned pieces).
 struct NoallocLayout {
-  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, pr32, pc32, q32, sp32, dx32, total;
+  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, pr32, pc32, q32, sp32, dx32, wv, pw32, total;
 };
 
 NoallocLayout noalloc_layout(const fct_plan P) {
@@ -1938,6 +2386,8 @@ NoallocLayout noalloc_layout(const fct_plan P) {
   L.q32 = take(sizeof(float) * R);
   L.sp32 = take(sizeof(float2) * N);
   L.dx32 = take(sizeof(float) * N);
+  L.wv = take(sizeof(float) * (P->hp.n_w_units > 0 ? 6 * N : 1));
+  L.pw32 = take(sizeof(float2) * 2 * std::max(P->hp.n_w_units, 1));
   L.total = off;
   return L;
 }
@@ -1986,6 +2436,8 @@ extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, dou
   hp.q32 = reinterpret_cast<float*>(b + L.q32);
   hp.sp32 = reinterpret_cast<float2*>(b + L.sp32);
   hp.dx32 = reinterpret_cast<float*>(b + L.dx32);
+  hp.wv = reinterpret_cast<float*>(b + L.wv);
+  hp.pw32 = reinterpret_cast<float2*>(b + L.pw32);
   DevPlan* dplan = reinterpret_cast<DevPlan*>(b + L.devplan);
   fct_report* drep = reinterpret_cast<fct_report*>(b + L.report);
   LaunchState* ls = reinterpret_cast<LaunchState*>(b + L.ls);

@@ -85,6 +85,17 @@ struct DevPlan {
   float* q32;                // [R]
   float2* sp32;              // [N] {s, p} of the inner FP32 solve
   float* dx32;               // [N]
+  // normal matrix W = A^T A of the mixed path's inner solve (n_w_units = 0:
+  // not built; the inner solve then applies A and A^T in two phases)
+  const int32_t* wrowptr;    // [N+1]
+  const int32_t* wcol;       // [nnz_w]
+  const float* wval;         // [nnz_w]
+  int32_t n_w_units;         // units of w_rows_per_unit consecutive rows
+  int32_t w_lanes;           // threads per row of W
+  int32_t w_rows_per_unit;   // = workers / w_lanes
+  int32_t pad_w;
+  float* wv;                 // [6N] w (two buffers), r, p, s, z of the pipelined CG
+  float2* pw32;              // [2 * n_w_units] partial (r.r, w.r), two buffers
   // condition estimate: when set, the FP64 solve starts from s = s_init (no
   // DCT, no b) and block 0 records (alpha_k, beta_k) of every CG iteration,
   // the Lanczos coefficients of A^T A for the start vector s_init
@@ -192,7 +203,7 @@ struct HostTables {
 // Validates inputs and builds all host tables.  Returns FCT_OK or an error with
 // the message in *err.
 fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
-                             const int32_t* sizes, const double* nodes, bool with_dct,
+                             const int32_t* sizes, const double* nodes, int grid_kind, bool with_dct,
                              HostTables* out, std::string* err);
 
 // Gather lanes of a row with len entries: min(32, pow2 >= ceil(len / epl)),
@@ -209,6 +220,13 @@ void device_row_order(HostTables* H, int epl);
 // workers / lanes consecutive rows of equal lane count.
 int64_t count_row_units(const HostTables& H, int workers, int epl);
 void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* first, std::vector<int32_t>* lanes);
+
+// W = A^T A (N x N, CSR, columns ascending, FP64 sums in a fixed order) and
+// the bound sum over rows of A of (row length)^2 >= nnz(W), cheap to compute
+// before deciding to build W.
+int64_t normal_matrix_bound(const HostTables& H);
+void normal_matrix(const HostTables& H, std::vector<int32_t>* rowptr, std::vector<int32_t>* col,
+                   std::vector<double>* val);
 
 // Per-row inputs of the fused last DCT pass (after device_row_order).
 void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::vector<int32_t>* rowk);

@@ -62,8 +62,27 @@ static inline int64_t fold_index(int64_t m, int64_t n) {
   return r <= n - 1 ? r : period - r;
 }
 
+// First-kind grid of n points (the aliasing lemma): with q = m div 2n and
+// r = m mod 2n, T_m's one entry in the n-row block is
+//   r < n: row r, (-1)^q (1 at r = 0, else 1/2);  r > n: row 2n - r, -(-1)^q / 2;
+//   r = n: none (T_m vanishes on every node) -- kept as row 0 with value 0.
+static inline int64_t fold_first_kind(int64_t m, int64_t n, double* val) {
+  const int64_t q = m / (2 * n), r = m % (2 * n);
+  const double sgn = (q & 1) ? -1.0 : 1.0;
+  if (r < n) {
+    *val = r == 0 ? sgn : 0.5 * sgn;
+    return r;
+  }
+  if (r > n) {
+    *val = -0.5 * sgn;
+    return 2 * n - r;
+  }
+  *val = 0.0;
+  return 0;
+}
+
 fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
-                             const int32_t* sizes, const double* nodes, bool with_dct,
+                             const int32_t* sizes, const double* nodes, int grid_kind, bool with_dct,
                              HostTables* out, std::string* err) {
   auto bad = [&](const std::string& m) {
     *err = m;
@@ -73,6 +92,8 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
   if (N < 1) return bad("N must be >= 1");
   if (K < 1) return bad("K must be >= 1");
   if (!support || !sizes) return bad("support and sizes must not be NULL");
+  if (grid_kind != FCT_GRID_EXTREMA && grid_kind != FCT_GRID_FIRST_KIND) return bad("unknown grid kind");
+  const bool first = grid_kind == FCT_GRID_FIRST_KIND;
   if (static_cast<int64_t>(K) * N >= (int64_t(1) << 31)) return bad("K*N must be below 2^31");
 
   HostTables& H = *out;
@@ -113,6 +134,16 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
   H.rowgrid.clear();
   H.rowptr.push_back(0);
 
+  // Nonzero components of every multi-index (axis order): a zero component
+  // folds to bin index 0 with entry 1 on every axis kind, so only nonzero
+  // components change a bin or an entry (sparse supports in high D have few).
+  std::vector<int64_t> nz_off(N + 1, 0);
+  std::vector<int32_t> nz_axis;
+  for (int64_t m = 0; m < N; ++m) {
+    for (int i = 0; i < D; ++i)
+      if (support[m * D + i] != 0) nz_axis.push_back(i);
+    nz_off[m + 1] = static_cast<int64_t>(nz_axis.size());
+  }
   std::vector<int64_t> stride(D);
   std::vector<int32_t> count;
   std::vector<int32_t> comp;
@@ -127,11 +158,16 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
       const uint16_t* mi = support + m * D;
       int64_t bidx = 0;
       double w = 1.0;
-      for (int i = 0; i < D; ++i) {
+      for (int64_t e = nz_off[m]; e < nz_off[m + 1]; ++e) {
+        const int i = nz_axis[e];
         const int32_t n = sz[i];
-        if (n >= 2) {
+        if (n >= 2 && first) {
+          double v = 0.0;
+          bidx += fold_first_kind(mi[i], n, &v) * stride[i];
+          w *= v;
+        } else if (n >= 2) {
           bidx += fold_index(mi[i], n) * stride[i];
-        } else if (mi[i] != 0) {
+        } else {
           const double xi = nodes ? nodes[l * D + i] : 1.0;
           w *= cheb_T(mi[i], xi);
         }
@@ -175,6 +211,8 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
       H.node_off[l * D + i] = static_cast<int32_t>(H.node_pos.size());
       if (n == 1) {
         H.node_pos.push_back(nodes ? nodes[l * D + i] : 1.0);
+      } else if (first) {
+        for (int j = 0; j < n; ++j) H.node_pos.push_back(cos_pi_ratio(2 * j + 1, 2 * static_cast<int64_t>(n)));
       } else {
         for (int j = 0; j < n; ++j) H.node_pos.push_back(cos_pi_ratio(j, n - 1));
       }
@@ -183,8 +221,10 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
 
   if (!with_dct) return FCT_OK;
 
-  // DCT-I interpolation matrices, one per distinct axis length:
-  //   C[k][j] = (2 e_k/(n-1)) e_j cos(pi (j k mod 2(n-1))/(n-1)),  e = 1/2 at the ends.
+  // DCT matrices, one per distinct axis length.  Extrema grid, the DCT-I
+  // interpolation: C[k][j] = (2 e_k/(n-1)) e_j cos(pi (j k mod 2(n-1))/(n-1)),
+  // e = 1/2 at the ends.  First-kind grid, the quadrature of the aliasing
+  // lemma: C[k][j] = cos(pi (k (2j + 1) mod 4n) / 2n) / n.
   std::vector<int32_t> mat_of(1, -1);
   auto matrix_for = [&](int32_t n) -> int32_t {
     if (static_cast<int32_t>(mat_of.size()) <= n) mat_of.resize(n + 1, -1);
@@ -192,6 +232,12 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
     const int32_t off = static_cast<int32_t>(H.dct_mats.size());
     if (n == 1) {
       H.dct_mats.push_back(1.0);
+    } else if (first) {
+      const int64_t h = 2 * static_cast<int64_t>(n);
+      for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j)
+          H.dct_mats.push_back(cos_pi_ratio((static_cast<int64_t>(k) * (2 * j + 1)) % (2 * h), h) /
+                               static_cast<double>(n));
     } else {
       const int64_t h = n - 1;
       for (int k = 0; k < n; ++k) {
@@ -236,7 +282,9 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
     }
     H.gfinal[l] = g;
   }
-  // Evaluation passes of the sampler: every active axis, E[j][k] = T_k(x_j),
+  // Evaluation passes of the sampler: every active axis, E[j][k] = T_k(x_j)
+  // (first-kind grid: times 2 for k > 0, since its bins hold T_k's
+  // coefficient halved),
   // pass p reads y0 (p = 0) or the previous output and the last pass writes
   // the caller's samples; a grid without active axes gets one copy pass.
   {
@@ -247,6 +295,12 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
       const int32_t off = static_cast<int32_t>(H.eval_mats.size());
       if (n == 1) {
         H.eval_mats.push_back(1.0);
+      } else if (first) {
+        const int64_t h = 2 * static_cast<int64_t>(n);
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k)
+            H.eval_mats.push_back((k == 0 ? 1.0 : 2.0) *
+                                  cos_pi_ratio((static_cast<int64_t>(k) * (2 * j + 1)) % (2 * h), h));
       } else {
         for (int j = 0; j < n; ++j)
           for (int k = 0; k < n; ++k)
@@ -405,6 +459,53 @@ void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::ve
   }
 }
 
+int64_t normal_matrix_bound(const HostTables& H) {
+  int64_t b = 0;
+  for (int64_t r = 0; r < H.R; ++r) {
+    const int64_t len = H.rowptr[r + 1] - H.rowptr[r];
+    b += len * len;
+  }
+  return b;
+}
+
+void normal_matrix(const HostTables& H, std::vector<int32_t>* rowptr, std::vector<int32_t>* col,
+                   std::vector<double>* val) {
+  // W[m][m'] = sum over grids l of w_l(m) * (entry of m' in the row of m on grid l);
+  // the grids are visited in order and each row in CSR order, so the sums have a
+  // fixed order.  Columns of a row come out ascending.
+  const int64_t N = H.N;
+  std::vector<double> acc(N, 0.0);
+  std::vector<char> mark(N, 0);
+  std::vector<int32_t> touched;
+  rowptr->assign(N + 1, 0);
+  col->clear();
+  val->clear();
+  for (int64_t m = 0; m < N; ++m) {
+    touched.clear();
+    for (int l = 0; l < H.K; ++l) {
+      const int64_t e = static_cast<int64_t>(l) * N + m;
+      const int32_t row = H.crow[e];
+      const double wm = H.weight[e];
+      for (int32_t j = H.rowptr[row]; j < H.rowptr[row + 1]; ++j) {
+        const int32_t c = H.col[j];
+        if (!mark[c]) {
+          mark[c] = 1;
+          touched.push_back(c);
+        }
+        acc[c] += wm * H.wcsr[j];
+      }
+    }
+    std::sort(touched.begin(), touched.end());
+    for (int32_t c : touched) {
+      col->push_back(c);
+      val->push_back(acc[c]);
+      acc[c] = 0.0;
+      mark[c] = 0;
+    }
+    (*rowptr)[m + 1] = static_cast<int32_t>(col->size());
+  }
+}
+
 }  // namespace fct
 
 extern "C" {
@@ -438,14 +539,16 @@ void fct_default_options(fct_options* opt) {
   opt->max_blocks = 0;
   opt->coef_lanes = 0;
   opt->timeout_s = 4.0;
+  opt->normal_matrix = 0;
+  opt->grid_kind = FCT_GRID_EXTREMA;
 }
 
 fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,
-                                 const int32_t* sizes, const double* nodes, int32_t* bin,
+                                 const int32_t* sizes, const double* nodes, int grid_kind, int32_t* bin,
                                  int32_t* crow, double* weight, int64_t* R_out) {
   fct::HostTables H;
   std::string err;
-  fct_status s = fct::build_host_tables(D, N, support, K, sizes, nodes, false, &H, &err);
+  fct_status s = fct::build_host_tables(D, N, support, K, sizes, nodes, grid_kind, false, &H, &err);
   if (s != FCT_OK) return fct::fail(s, err);
   const size_t KN = static_cast<size_t>(K) * static_cast<size_t>(N);
   if (bin) std::memcpy(bin, H.bin.data(), KN * sizeof(int32_t));

@@ -25,6 +25,8 @@ FCT_ERR_NO_DEVICE = 8
 
 FCT_FP64 = 0
 FCT_MIXED = 1
+FCT_GRID_EXTREMA = 0
+FCT_GRID_FIRST_KIND = 1
 
 FCT_FAMILY_POLY = 0
 FCT_FAMILY_GAUSSCOS = 1
@@ -44,6 +46,8 @@ class fct_options(ctypes.Structure):
         ("max_blocks", ctypes.c_int),
         ("coef_lanes", ctypes.c_int),
         ("timeout_s", ctypes.c_double),
+        ("normal_matrix", ctypes.c_int),
+        ("grid_kind", ctypes.c_int),
     ]
 
 
@@ -74,6 +78,7 @@ class fct_plan_info(ctypes.Structure):
         ("block_threads", ctypes.c_int32),
         ("coef_lanes", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
+        ("normal_nnz", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -106,6 +111,7 @@ SIGNATURES = [
     ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
     ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
+    ("fct_evaluate", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), _P]),
@@ -117,8 +123,8 @@ SIGNATURES = [
     ("fct_server_destroy", ctypes.c_int, [_P]),
     ("fct_selftest_wait_timeout", ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(ctypes.c_double)]),
-    ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, _P, _P, _P,
-                                             ctypes.POINTER(ctypes.c_int64)]),
+    ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P,
+                                             _P, _P, ctypes.POINTER(ctypes.c_int64)]),
 ]
 
 
@@ -305,6 +311,12 @@ def fct_plan_condition(plan: int, start, work, iterations: int = 200, stream=Non
     return {"kappa": k.value, "lambda_min": lo.value, "lambda_max": hi.value, "iterations": used.value}
 
 
+def fct_evaluate(plan: int, coeffs, points, values, stream=None):
+    """values[p] = sum_m coeffs[m] prod_i T_{m_i}(points[p, i]) (device buffers)."""
+    n = int(points.shape[0]) if hasattr(points, "shape") else 0
+    _check(lib().fct_evaluate(plan, _ptr(coeffs), n, _ptr(points), _ptr(values), _stream(stream)))
+
+
 def fct_plan_clone(plan: int) -> int:
     h = _P()
     _check(lib().fct_plan_clone(ctypes.byref(h), plan))
@@ -349,7 +361,8 @@ def fct_destroy(plan: int):
         _check(lib().fct_destroy(plan))
 
 
-def fct_alias_tables_host(support: np.ndarray, sizes: np.ndarray, nodes: np.ndarray | None = None):
+def fct_alias_tables_host(support: np.ndarray, sizes: np.ndarray, nodes: np.ndarray | None = None,
+                          grid_kind: int = 0):
     """Host-only alias tables: (bin int32[K,N], crow int32[K,N], weight f64[K,N], R)."""
     support = np.ascontiguousarray(support, dtype=np.uint16)
     sizes = np.ascontiguousarray(sizes, dtype=np.int32)
@@ -361,8 +374,8 @@ def fct_alias_tables_host(support: np.ndarray, sizes: np.ndarray, nodes: np.ndar
     c = np.zeros((K, N), dtype=np.int32)
     w = np.zeros((K, N), dtype=np.float64)
     R = ctypes.c_int64()
-    _check(lib().fct_alias_tables_host(D, N, _ptr(support), K, _ptr(sizes), _ptr(nodes), _ptr(b), _ptr(c), _ptr(w),
-                                       ctypes.byref(R)))
+    _check(lib().fct_alias_tables_host(D, N, _ptr(support), K, _ptr(sizes), _ptr(nodes), grid_kind, _ptr(b), _ptr(c),
+                                       _ptr(w), ctypes.byref(R)))
     return b, c, w, int(R.value)
 
 
@@ -398,6 +411,9 @@ class Plan:
 
     def execute(self, samples, coeffs, stream=None, report=True):
         return fct_execute(self.handle, samples, coeffs, stream, report)
+
+    def evaluate(self, coeffs, points, values, stream=None):
+        fct_evaluate(self.handle, coeffs, points, values, stream)
 
     def execute_host(self, samples_host, coeffs_host, stream=None):
         return fct_execute_host(self.handle, samples_host, coeffs_host, stream)

@@ -66,6 +66,40 @@ def test_alias_tables_bit_exact_vs_oracle(lib, name, mk):
         assert np.max(np.abs(wt[l] - ow)) <= 1e-13
 
 
+FIRST_CASES = [
+    ("small", lambda: W.config_small_poly()),
+    ("d3", lambda: W.make_workload("t", 11, 3, 6, 6, 1, 7, W.FAMILY_GAUSSCOS)),
+    ("d6", lambda: W.config_d6_gausscos()),
+    ("d1", lambda: W.make_workload("t1", 61, 1, 14, 6, 4, 11, W.FAMILY_POLY)),
+]
+
+
+@pytest.mark.parametrize("name,mk", FIRST_CASES, ids=[c[0] for c in FIRST_CASES])
+def test_first_kind_alias_tables_bit_exact_vs_oracle(lib, name, mk):
+    """The paper's first-kind grid: signed 1, +-1/2, 0 entries (exact in
+    FP64, so compared bitwise where no single-point weight enters)."""
+    w = mk()
+    b, c, wt, R = F.fct_alias_tables_host(w.support, w.sizes, w.nodes, grid_kind=F.FCT_GRID_FIRST_KIND)
+    s = O.AliasSystem(w.support, w.sizes, w.nodes, kind="first")
+    assert R == s.R
+    off = 0
+    for l in range(w.K):
+        ob = O.grid_bins_first_kind(w.support, w.sizes[l])
+        assert np.array_equal(b[l], ob)
+        assert np.array_equal(c[l], off + np.searchsorted(s.rows[l], ob))
+        off += len(s.rows[l])
+        ow = O.grid_weights_first_kind(w.support, w.sizes[l], w.nodes[l])
+        if np.all(w.sizes[l] >= 2):
+            assert np.array_equal(wt[l], ow)
+        assert np.max(np.abs(wt[l] - ow)) <= 1e-13
+
+
+def test_unknown_grid_kind_rejected(lib):
+    w = W.config_small_poly()
+    with pytest.raises(F.FctError):
+        F.fct_alias_tables_host(w.support, w.sizes, w.nodes, grid_kind=7)
+
+
 def test_alias_tables_reject_bad_input(lib):
     sup = np.zeros((3, 2), dtype=np.uint16)
     with pytest.raises(F.FctError):

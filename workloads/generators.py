@@ -37,6 +37,7 @@ _PURPOSE = {
     "batch": 5,      # per-transform shapes inside a batch
     "arrivals": 6,   # serving arrival process
     "probe": 7,      # start vectors of condition probes and test matrices
+    "support": 8,    # random sparse supports
 }
 
 
@@ -63,6 +64,44 @@ def total_degree_support(D: int, d: int) -> np.ndarray:
         rows = np.concatenate([np.repeat(rows, counts, axis=0), vals[:, None]], axis=1)
         rem = np.repeat(rem, counts) - vals
     return rows.astype(np.uint16)
+
+
+def euclidean_support(D: int, d: int) -> np.ndarray:
+    """All n in N^D with |n|_2 <= d (the Euclidean index set S^2_{d,D} of
+    Sec. 2), lexicographic, uint16[N, D]: the total-degree set filtered by the
+    integer test sum n_i^2 <= d^2 (|n|_2 <= d implies |n|_1 <= d sqrt(D))."""
+    cap = int(np.floor(d * np.sqrt(D))) + 1
+    rows = np.zeros((1, 0), dtype=np.int64)
+    sq = np.zeros(1, dtype=np.int64)
+    for _ in range(D):
+        vals = np.arange(min(d, cap) + 1, dtype=np.int64)
+        ok = sq[:, None] + vals[None, :] ** 2 <= d * d
+        r_idx, v_idx = np.nonzero(ok)
+        rows = np.concatenate([rows[r_idx], vals[v_idx][:, None]], axis=1)
+        sq = sq[r_idx] + vals[v_idx] ** 2
+    return rows.astype(np.uint16)
+
+
+def sparse_infinity_support(seed: int, D: int, d: int, N: int, nonzeros: int) -> np.ndarray:
+    """N distinct multi-indices of S^inf_{d,D} (max degree d), each with
+    exactly `nonzeros` nonzero components at uniformly drawn axes with values
+    uniform in {1..d}, plus the zero index; sorted lexicographically.  (The
+    paper's sparse-support family draws N multi-indices of S^inf_{d,D} at
+    random; `nonzeros` fixes how many components of each are nonzero.)"""
+    g = stream(seed, "support")
+    seen = {tuple([0] * D)}
+    out = [np.zeros(D, dtype=np.int64)]
+    while len(out) < N:
+        m = np.zeros(D, dtype=np.int64)
+        axes = g.choice(D, size=nonzeros, replace=False)
+        m[axes] = g.integers(1, d + 1, size=nonzeros)
+        t = tuple(m.tolist())
+        if t not in seen:
+            seen.add(t)
+            out.append(m)
+    arr = np.stack(out)
+    order = np.lexsort(arr.T[::-1])
+    return arr[order].astype(np.uint16)
 
 
 # --------------------------------------------------------------------------
