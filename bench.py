@@ -39,6 +39,8 @@ SERVING_RATES = "25,100,1000,5000"
 SERVING_REQUESTS = 200
 SERVING_KAPPA0 = 20.0
 SERVING_VARIANTS = 4         # Gaussian-cosine inputs per serving shape (plus one polynomial)
+BATCH = 38                   # batched leg: transforms of the bench workload per launch
+ACCURACY_POINTS = 5000       # random points of the L-infinity error of the approximation
 
 
 def parse():
@@ -55,6 +57,8 @@ def parse():
     ap.add_argument("--serving-kappa0", type=float, default=SERVING_KAPPA0,
                     help="Algorithm 2 bound on kappa(A) used to pick each serving shape's grid count")
     ap.add_argument("--serving-team-blocks", type=int, default=16)
+    ap.add_argument("--batch", type=int, default=BATCH, help="transforms per launch of the batched leg (0 = skip)")
+    ap.add_argument("--batch-team-blocks", type=int, default=16)
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=CPU_BUDGET_S, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-fraction", type=float, default=1.0, help=argparse.SUPPRESS)
@@ -331,7 +335,13 @@ def run_gpu(args):
         results[prec] = dict(plan_info=plan.info, rep=rep, rep_last=rep_last, coeffs=c_first,
                              step_ms=step_ms, total_s=total_s, t_wall=t_wall, clocks=clk, deterministic=same,
                              e2e_s=e2e_s, e2e_host_equal=bool(np.array_equal(c_host.numpy(), c_first)))
+        if prec == "mixed":
+            results[prec]["accuracy"] = approximation_error(F, plan, w, torch.from_numpy(c_first).cuda())
         plan.close()
+
+    batched = run_batched(args, F, w, opts["mixed"], flush) if args.batch > 0 else None
+    if batched is not None and world > 1:
+        batched["total_s"] = max_over_ranks(batched["total_s"], device="cuda")
 
     serving = run_serving(args, F) if rank == 0 and world == 1 else None
 
@@ -391,6 +401,11 @@ def run_gpu(args):
                           "rel_err_vs_oracle": r["rel_err"], "deterministic": r["deterministic"],
                           "e2e_value": w.N / r["e2e_s"]} for p, r in results.items()},
     }
+    if "accuracy" in results.get("mixed", {}):
+        line["accuracy"] = results["mixed"]["accuracy"]
+    if batched is not None:
+        batched["value"] = whole_job_value(batched["coeffs_per_launch"], args.steps, world, batched["total_s"])
+        line["batched"] = batched
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:
@@ -403,6 +418,71 @@ def run_gpu(args):
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched leg and approximation error
+# ---------------------------------------------------------------------------
+def approximation_error(F, plan, w, coeffs_dev) -> dict:
+    """L-infinity error of the computed expansion against the target at random
+    points of [-1, 1]^D (the paper's accuracy measure), evaluated on the
+    device by fct_evaluate; the target itself is evaluated on the host."""
+    import numpy as np
+    import torch
+    import workloads as W
+    pts = W.stream(17, "probe").uniform(-1.0, 1.0, (ACCURACY_POINTS, w.D))
+    vals = torch.empty(ACCURACY_POINTS, dtype=torch.float64, device="cuda")
+    plan.evaluate(coeffs_dev, torch.from_numpy(pts).cuda(), vals)
+    torch.cuda.synchronize()
+    a, b = w.params[:w.D], w.params[w.D:2 * w.D]
+    f = np.exp(-(pts ** 2) @ a) * np.cos(pts @ b)
+    err = np.abs(vals.cpu().numpy() - f)
+    return {"linf_abs_error": float(err.max()), "points": ACCURACY_POINTS,
+            "note": "max |p(x) - f(x)| of the mixed-path expansion at uniform random points"}
+
+
+def run_batched(args, F, w, opts, flush) -> dict:
+    """B transforms of the bench workload (distinct Gaussian-cosine targets,
+    one plan and B - 1 clones) per launch of fct_execute_batch, teams of
+    args.batch_team_blocks blocks; L2 flushed between launches."""
+    import statistics as st
+    import torch
+    import workloads as W
+    B = args.batch
+    base = F.Plan(w.support, w.sizes, w.nodes, **opts)
+    plans = [base] + [base.clone() for _ in range(B - 1)]
+    xs, cs = [], []
+    for i in range(B):
+        x = torch.empty(base.M, dtype=torch.float64, device="cuda")
+        base.sample(w.family, W.gausscos_params(1000 + i, w.D), x)
+        xs.append(x)
+        cs.append(torch.empty(base.N, dtype=torch.float64, device="cuda"))
+    hs = [p.handle for p in plans]
+    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks)
+    alone = torch.empty(base.N, dtype=torch.float64, device="cuda")
+    base.execute(xs[B - 1], alone)
+    same = bool(torch.equal(alone, cs[B - 1]))
+    for _ in range(args.warmup):
+        F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks, report=False)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks, report=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    for p in plans[1:]:
+        p.close()
+    base.close()
+    return {"transforms_per_launch": B, "team_blocks": args.batch_team_blocks, "path": "mixed",
+            "coeffs_per_launch": B * w.N, "ms_per_launch": st.mean(ms), "total_s": sum(ms) / 1e3,
+            "all_converged": all(r["status"] == 0 for r in reps),
+            "max_iterations": max(r["iterations"] for r in reps),
+            "batch_equals_alone": same, "unit": UNIT,
+            "note": "independent transforms of the bench workload in one persistent launch (fct_execute_batch)"}
 
 
 # ---------------------------------------------------------------------------

@@ -508,3 +508,21 @@ def test_evaluate_at_grid_points_equals_recurrence_sampler():
     got = O.evaluate_expansion(w.coeffs_true, w.support, pts)
     want = O.sample_poly_bruteforce(w.coeffs_true, w.support, axes).ravel()
     assert np.allclose(got, want, atol=1e-13)
+
+
+# ---------------------------------------------------------------- other supports (generators)
+@pytest.mark.parametrize("D,d", [(1, 7), (2, 50), (3, 9), (5, 6)])
+def test_euclidean_support_is_the_l2_ball(D, d):
+    sup = W.euclidean_support(D, d)
+    brute = np.array([m for m in itertools.product(range(d + 1), repeat=D) if sum(x * x for x in m) <= d * d],
+                     dtype=np.uint16)
+    assert np.array_equal(sup, brute)
+
+
+def test_sparse_infinity_support_properties():
+    sup = W.sparse_infinity_support(3, 40, 9, 3000, 3)
+    assert sup.shape == (3000, 40) and sup.max() <= 9
+    assert len({tuple(r) for r in sup.tolist()}) == 3000
+    nz = (sup > 0).sum(axis=1)
+    assert nz[0] == 0 and np.all(nz[1:] == 3)
+    assert np.array_equal(sup, sup[np.lexsort(sup.T[::-1])])
