@@ -98,6 +98,16 @@ typedef struct {
                          and the signed entries 1, +-1/2, 0 of Eq. (aliasing_matrix_1d)
                          (Lemma lem:aliasing), multiplied over axes.  Single-point
                          axes sample the given node in both kinds.                  */
+  int cluster_solve;  /* FCT_MIXED: 1 = after the DCT and b (whole GPU), run the solve in one
+                         thread-block cluster (16 blocks, one per SM) whose blocks hold
+                         the FP32 tables and the vectors in shared memory, gather
+                         through distributed shared memory and synchronise with
+                         cluster barriers; used by fct_execute / fct_execute_host
+                         when every block's slice fits (fct_plan_info.cluster_blocks
+                         says whether it does), else the team solver.  0 (default) =
+                         team solver.  Batches, serving and fct_execute_noalloc use
+                         the team solver.  With normal_matrix = 0 (auto), asking for
+                         the cluster solver keeps the plan from storing W.           */
 } fct_options;
 
 typedef struct {
@@ -121,6 +131,7 @@ typedef struct {
   int32_t coef_lanes;
   int64_t device_bytes;     /* tables + workspace held on the device               */
   int64_t normal_nnz;       /* nonzeros of W = A^T A when the plan stores it, else 0 */
+  int64_t cluster_blocks;   /* blocks of the cluster solver fct_execute uses, else 0 */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,

@@ -96,6 +96,14 @@ struct DevPlan {
   int32_t pad_w;
   float* wv;                 // [6N] w (two buffers), r, p, s, z of the pipelined CG
   float2* pw32;              // [2 * n_w_units] partial (r.r, w.r), two buffers
+  // cluster solver of the mixed path (cl_cs = 0: not set up): one thread-block
+  // cluster holds the FP32 tables and the Krylov vectors in distributed shared
+  // memory; rows are split by entry count, coefficients in chunks of cl_nc
+  const int32_t* cl_rows;    // [cl_cs + 1] first row of every block of the cluster
+  int32_t cl_cs;             // blocks per cluster
+  int32_t cl_nc;             // coefficients per block
+  int32_t cl_maxrows;        // most rows of one block
+  int32_t cl_w_smem;         // 1: FP32 entry values staged in shared memory too
   // condition estimate: when set, the FP64 solve starts from s = s_init (no
   // DCT, no b) and block 0 records (alpha_k, beta_k) of every CG iteration,
   // the Lanczos coefficients of A^T A for the start vector s_init
@@ -114,10 +122,11 @@ struct SolveJob {
   int32_t precision;
   int32_t max_iter;
   int32_t max_refine;
-  int32_t pad;
+  int32_t flags;             // kJobPrepareOnly: stop after s = A^T b (the cluster solver continues)
   double tol;
   double inner_tol;
 };
+constexpr int32_t kJobPrepareOnly = 1;
 
 // Barrier of one team: a monotonic arrival counter (target = G x barrier
 // number) and an exit counter that lets the last block reset it.

@@ -541,6 +541,7 @@ void fct_default_options(fct_options* opt) {
   opt->timeout_s = 4.0;
   opt->normal_matrix = 0;
   opt->grid_kind = FCT_GRID_EXTREMA;
+  opt->cluster_solve = 0;
 }
 
 fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,

@@ -48,6 +48,7 @@ class fct_options(ctypes.Structure):
         ("timeout_s", ctypes.c_double),
         ("normal_matrix", ctypes.c_int),
         ("grid_kind", ctypes.c_int),
+        ("cluster_solve", ctypes.c_int),
     ]
 
 
@@ -79,6 +80,7 @@ class fct_plan_info(ctypes.Structure):
         ("coef_lanes", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
         ("normal_nnz", ctypes.c_int64),
+        ("cluster_blocks", ctypes.c_int64),
     ]
 
     def as_dict(self):
