@@ -98,6 +98,12 @@ typedef struct {
                          and the signed entries 1, +-1/2, 0 of Eq. (aliasing_matrix_1d)
                          (Lemma lem:aliasing), multiplied over axes.  Single-point
                          axes sample the given node in both kinds.                  */
+  int entries_per_lane; /* A p gather: 0 = auto (the fewest entries per lane, of 2, 4 or 8,
+                         whose row units fit one wave of co-resident blocks: lowest
+                         latency for one transform on the whole GPU); 2, 4 or 8 fixes
+                         it.  Larger values mean fewer, longer units: better when
+                         the plan runs on small teams (fct_execute_batch, serving),
+                         where a block works through many units one after another. */
   int cluster_solve;  /* FCT_MIXED: 1 = after the DCT and b (whole GPU), run the solve in one
                          thread-block cluster (16 blocks, one per SM) whose blocks hold
                          the FP32 tables and the vectors in shared memory, gather
@@ -297,7 +303,9 @@ fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* 
  * lower bound on kappa(A) that tightens as iterations grow (the CG
  * coefficients carry FP32-reduced norms, so the estimate resolves kappa up to
  * about 1e3); *used = iterations recorded (fewer when the iteration breaks
- * down).  Outputs other than kappa may be NULL.  Synchronous.
+ * down or the normal residual has fallen by 1e12, by which point the extreme
+ * Ritz values have converged).  Outputs other than kappa may be NULL.
+ * Synchronous.
  */
 fct_status fct_plan_condition(fct_plan plan, const double* start, double* work, int iterations,
                               double* kappa, double* lambda_min, double* lambda_max, int* used, void* stream);

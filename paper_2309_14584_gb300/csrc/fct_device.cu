@@ -2210,6 +2210,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     return fail(FCT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
   if (o.coef_lanes != 0 && (o.coef_lanes < 1 || o.coef_lanes > 16 || (o.coef_lanes & (o.coef_lanes - 1))))
     return fail(FCT_ERR_INVALID_ARG, "coef_lanes must be 0 or a power of two <= 16");
+  if (o.entries_per_lane != 0 && o.entries_per_lane != 2 && o.entries_per_lane != 4 && o.entries_per_lane != 8)
+    return fail(FCT_ERR_INVALID_ARG, "entries_per_lane must be 0, 2, 4 or 8");
   int ndev = 0;
   cudaError_t ce = cudaGetDeviceCount(&ndev);
   if (ce != cudaSuccess || ndev < 1) return fail(FCT_ERR_NO_DEVICE, "no CUDA device");
@@ -2271,6 +2273,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
           epl = e;
           break;
         }
+      if (o.entries_per_lane > 0) epl = o.entries_per_lane;
     }
   }
   device_row_order(&H, epl);
@@ -3259,7 +3262,10 @@ extern "C" fct_status fct_plan_condition(fct_plan P, const double* start, double
   a.single.plan = dplan;
   a.single.precision = FCT_FP64;
   a.single.max_iter = iterations;
-  a.single.tol = 0.0;
+  // Stop once the normal residual has fallen by 1e12: the extreme Ritz values
+  // have converged by then, and further iterations would take alpha and beta
+  // from relative squares below FP32's normal range, where they lose precision.
+  a.single.tol = 1e-12;
   a.jobs = nullptr;
   a.njobs = 1;
   a.team_blocks = P->grid_blocks;

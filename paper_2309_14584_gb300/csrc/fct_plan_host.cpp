@@ -541,6 +541,7 @@ void fct_default_options(fct_options* opt) {
   opt->timeout_s = 4.0;
   opt->normal_matrix = 0;
   opt->grid_kind = FCT_GRID_EXTREMA;
+  opt->entries_per_lane = 0;
   opt->cluster_solve = 0;
 }
 

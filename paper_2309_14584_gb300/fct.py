@@ -48,6 +48,7 @@ class fct_options(ctypes.Structure):
         ("timeout_s", ctypes.c_double),
         ("normal_matrix", ctypes.c_int),
         ("grid_kind", ctypes.c_int),
+        ("entries_per_lane", ctypes.c_int),
         ("cluster_solve", ctypes.c_int),
     ]
 

@@ -94,3 +94,16 @@ def test_select_grids_reports_exhaustion():
     sup, sizes, nodes = _cands(K=8)
     r = lgrid.select_grids(sup, sizes, nodes, kappa0=2.0, step=3, probe_iterations=36)
     assert r["L"] is None and r["kappa"] > 2.0
+
+
+def test_condition_estimate_past_convergence_stays_exact():
+    """More probe iterations than CG needs to converge (D=4, degree 8, 12
+    grids: converged in well under 100): the estimate must not drift once the
+    residual is tiny (it stops at a 1e12 reduction)."""
+    sup = W.total_degree_support(4, 8)
+    sizes, nodes = W.l_grid(21, sup.shape[0], 4, 12, 1, 9)
+    A = O.AliasSystem(sup, sizes, nodes).A.toarray()
+    sv = np.linalg.svd(A, compute_uv=False)
+    r = lgrid.probe_condition(sup, sizes, nodes, iterations=400)
+    assert r["iterations"] < 400
+    assert r["kappa"] == pytest.approx(sv[0] / sv[-1], rel=1e-3)
