@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=SERVING_REQUESTS, help="requests per rate")
     ap.add_argument("--serving-kappa0", type=float, default=SERVING_KAPPA0,
                     help="Algorithm 2 bound on kappa(A) used to pick each serving shape's grid count")
-    ap.add_argument("--serving-team-blocks", type=int, default=16)
+    ap.add_argument("--serving-team-blocks", type=int, default=38)
     ap.add_argument("--batch", type=int, default=BATCH, help="transforms per launch of the batched leg (0 = skip)")
     ap.add_argument("--batch-team-blocks", type=int, default=16)
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)

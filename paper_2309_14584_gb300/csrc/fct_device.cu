@@ -57,7 +57,10 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
 
-// Loads of data written earlier in the same launch by other blocks bypass L1.
+// Loads of data written earlier in the same launch by other blocks bypass L1
+// (ldcg), except the CG gathers of {s, p} and q: those vectors change only in
+// the phase before a team barrier, and the barrier's gpu-scope acquire drops
+// the SM's L1 lines, so plain loads are current and repeated sectors hit L1.
 template <typename T>
 __device__ __forceinline__ T ldcg(const T* p) {
   return __ldcg(p);
@@ -539,7 +542,9 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
       V2 v[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        if (c[i] >= 0) v[i] = ldcg(sp + c[i]);
+        // plain (L1-cached) loads: {s, p} is written only in the phase before
+        // the last team barrier, whose acquire drops this SM's stale L1 lines
+        if (c[i] >= 0) v[i] = sp[c[i]];
         else { v[i].x = V(0); v[i].y = V(0); }
       }
 #pragma unroll
@@ -753,7 +758,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       if (wk >= 0) {
         if (c < ncc) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
+          t = coef_gather<V, WT>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
         }
       } else {
         const float dl = warp0_team_sum_f(P.pr32, nru);
@@ -778,7 +783,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       for (; c < ncc; c += tm.G, ++k) {
         if (k > 0 && wk >= 0) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(q + i); });
+          t = coef_gather<V, WT>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
         float part = 0.0f;
         if (wk >= 0 && lead) {

@@ -165,6 +165,20 @@ def test_launch_shapes_agree(bt, lanes, blocks):
     assert rel(got, ref) <= TOL_FP64
 
 
+@pytest.mark.parametrize("epl", [2, 4, 8])
+def test_entries_per_lane_agree(epl):
+    """Fixed gather granularity (fewer, longer row units) gives the same
+    answer as the automatic choice, within tolerance of the oracle."""
+    w = _small(SMALL[4])
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+    for prec in (F.FCT_FP64, F.FCT_MIXED):
+        got, _, rep = gpu_run(w, samples_np=f, tol=1e-14 if prec == F.FCT_FP64 else 1e-12, inner_tol=1e-5,
+                              precision=prec, entries_per_lane=epl, coef_lanes=1)
+        assert rep["status"] == 0
+        assert rel(got, ref) <= (TOL_FP64 if prec == F.FCT_FP64 else TOL_MIXED)
+
+
 def test_edge_single_coefficient_and_single_point_grid():
     """N = 1 (support {0}) on grids that are single points: c* = mean-free LS
     of the constant, i.e. the average of the samples weighted as one row per grid."""
