@@ -284,15 +284,23 @@ struct BlockTabs {
   const int* hdrW;      // [nW][2] {entries, pool offset}
   const int* pool;
   int cachedA, cachedB, cachedW;
+  int wbytes;           // entry values staged with the A / B units: 4 (FP32), 8 (FP64) or 0
   const double* mats;   // DCT matrices (shared copy or global)
 };
+
+// Start (in ints, from the unit's pool offset) of a unit's staged entry
+// values: after n index ints, rounded up to 8 bytes.
+__device__ __forceinline__ int wt_start(int off, int n) { return (off + n + 1) & ~1; }
 
 //   W units (rows of A^T A, mixed path only; staged first, since the inner
 //   solve runs most often): pool holds rowptr[m0..m1] - jbase, the columns,
 //   then the FP32 values (as bits).
+//   wbytes = 4 / 8: the A and B units also hold the entry values the CG loop
+//   reads (FP32 for the mixed path's inner solve, FP64 for the FP64 path),
+//   8-byte aligned after the indices.
 template <int BT>
 __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char* dsm, int smem_bytes, BlockTabs* T,
-                                bool with_w) {
+                                bool with_w, int wbytes) {
   const int nru = P.n_row_units, ncc = P.n_coef_chunks, nwu = with_w ? P.n_w_units : 0;
   const int nA = nru > tm.rank ? (nru - tm.rank + tm.G - 1) / tm.G : 0;
   const int nB = ncc > tm.rank ? (ncc - tm.rank + tm.G - 1) / tm.G : 0;
@@ -308,8 +316,10 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   int* hdrA = reinterpret_cast<int*>(dsm + off);
   int* hdrB = hdrA + 5 * nA;
   int* hdrW = hdrB + nB;
-  int* pool = hdrW + 2 * nW;
-  const int cap = (smem_bytes - off) / 4 - 5 * nA - nB - 2 * nW;  // ints left for the pool
+  const int nhdr = (5 * nA + nB + 2 * nW + 1) & ~1;  // the pool starts 8-byte aligned
+  int* pool = hdrA + nhdr;
+  const int cap = (smem_bytes - off) / 4 - nhdr;  // ints left for the pool
+  const int wi = wbytes / 4;  // ints per staged entry value
   int used = 0, cachedA = 0, cachedB = 0, cachedW = 0;
   if (cap > 0) {
     for (int k = 0; k < nW; ++k) {
@@ -336,12 +346,20 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
       const int u = tm.rank + k * tm.G;
       const int r0 = __ldg(P.ru_first + u), r1 = __ldg(P.ru_first + u + 1);
       const int jbase = __ldg(P.rowptr + r0), jend = __ldg(P.rowptr + r1);
-      const int need = (r1 - r0 + 1) + (jend - jbase);
+      const int nidx = (r1 - r0 + 1) + (jend - jbase);
+      const int need = wi ? wt_start(used, nidx) - used + wi * (jend - jbase) : nidx;
       if (used + need > cap) break;
       int* rp = pool + used;
       for (int i = threadIdx.x; i <= r1 - r0; i += BT) rp[i] = __ldg(P.rowptr + r0 + i) - jbase;
       int* cl = rp + (r1 - r0 + 1);
       for (int i = threadIdx.x; i < jend - jbase; i += BT) cl[i] = __ldg(P.col + jbase + i);
+      if (wi == 1) {
+        float* wv = reinterpret_cast<float*>(pool + wt_start(used, nidx));
+        for (int i = threadIdx.x; i < jend - jbase; i += BT) wv[i] = __ldg(P.wcsr32 + jbase + i);
+      } else if (wi == 2) {
+        double* wv = reinterpret_cast<double*>(pool + wt_start(used, nidx));
+        for (int i = threadIdx.x; i < jend - jbase; i += BT) wv[i] = __ldg(P.wcsr + jbase + i);
+      }
       if (threadIdx.x == 0) {
         int* h = hdrA + 5 * k;
         h[0] = r0;
@@ -357,13 +375,27 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
     const int64_t N = P.N;
     for (int k = 0; k < nB; ++k) {
       const int c = tm.rank + k * tm.G;
-      const int need = P.K * cpc;
+      const int nidx = P.K * cpc;
+      const int need = wi ? wt_start(used, nidx) - used + wi * nidx : nidx;
       if (used + need > cap) break;
       int* cr = pool + used;
       const int m0 = c * cpc;
-      for (int i = threadIdx.x; i < need; i += BT) {
+      for (int i = threadIdx.x; i < nidx; i += BT) {
         const int l = i / cpc, mm = m0 + i % cpc;
         cr[i] = mm < P.N ? __ldg(P.crow + l * N + mm) : 0;
+      }
+      if (wi == 1) {
+        float* wv = reinterpret_cast<float*>(pool + wt_start(used, nidx));
+        for (int i = threadIdx.x; i < nidx; i += BT) {
+          const int l = i / cpc, mm = m0 + i % cpc;
+          wv[i] = mm < P.N ? __ldg(P.wcm32 + l * N + mm) : 0.0f;
+        }
+      } else if (wi == 2) {
+        double* wv = reinterpret_cast<double*>(pool + wt_start(used, nidx));
+        for (int i = threadIdx.x; i < nidx; i += BT) {
+          const int l = i / cpc, mm = m0 + i % cpc;
+          wv[i] = mm < P.N ? __ldg(P.wcm + l * N + mm) : 0.0;
+        }
       }
       if (threadIdx.x == 0) hdrB[k] = used;
       used += need;
@@ -378,6 +410,7 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   T->cachedA = cachedA;
   T->cachedB = cachedB;
   T->cachedW = cachedW;
+  T->wbytes = wbytes;
   T->mats = mats;
 }
 
@@ -432,8 +465,10 @@ struct RowUnit {
   int r0, r1, lc, jbase;
   const int* rp;   // shared rowptr - jbase (nullptr: global)
   const int* cl;   // shared col (relative to jbase)
+  const void* wt;  // shared entry values (T.wbytes each, relative to jbase), or nullptr
 };
 
+template <bool SV>
 __device__ __forceinline__ RowUnit row_unit_geom(const DevPlan& P, const BlockTabs& T, int u, int k) {
   RowUnit g;
   if (k < T.cachedA) {
@@ -444,6 +479,11 @@ __device__ __forceinline__ RowUnit row_unit_geom(const DevPlan& P, const BlockTa
     g.jbase = h[3];
     g.rp = T.pool + h[4];
     g.cl = g.rp + (g.r1 - g.r0 + 1);
+    if constexpr (SV)
+      g.wt = T.wbytes ? static_cast<const void*>(T.pool + wt_start(h[4], (g.r1 - g.r0 + 1) + g.rp[g.r1 - g.r0]))
+                      : nullptr;
+    else
+      g.wt = nullptr;
   } else {
     g.r0 = __ldg(P.ru_first + u);
     g.r1 = __ldg(P.ru_first + u + 1);
@@ -451,17 +491,19 @@ __device__ __forceinline__ RowUnit row_unit_geom(const DevPlan& P, const BlockTa
     g.jbase = 0;
     g.rp = nullptr;
     g.cl = nullptr;
+    g.wt = nullptr;
   }
   return g;
 }
 
 // Row gather: for each value functor, sum over the row's entries of
 // w_j * val(col_j).  Entries are staged four per lane at a time.
-template <typename V, typename WT, int NV, typename Val1, typename Val2>
+template <typename V, typename WT, int NV, bool SV, typename Val1, typename Val2>
 __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
                                             int k, int wk, int* row_out, bool* lead, Val1 val1, Val2 val2, V* out1,
                                             V* out2) {
-  const RowUnit g = row_unit_geom(P, T, u, k);
+  const RowUnit g = row_unit_geom<SV>(P, T, u, k);
+  const bool ws = SV && g.wt != nullptr && static_cast<int>(sizeof(WT)) == T.wbytes;
   const int row = g.r0 + wk / g.lc;
   const int lane = wk & (g.lc - 1);
   V a1 = V(0), a2 = V(0);
@@ -481,7 +523,7 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
       for (int i = 0; i < 4; ++i) {
         const int j = j0 + i * g.lc;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
-        wv[i] = j < jb ? __ldg(w + g.jbase + j) : WT(0);
+        wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
       V v1[4], v2[4];
 #pragma unroll
@@ -503,21 +545,22 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
   *lead = (row < g.r1) && lane == 0;
 }
 
-template <typename V, typename WT, typename Val>
+template <typename V, typename WT, bool SV, typename Val>
 __device__ __forceinline__ V row_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u, int k,
                                         int wk, int* row_out, bool* lead, Val val) {
   V a, b;
-  row_gather_n<V, WT, 1>(P, T, w, u, k, wk, row_out, lead, val, val, &a, &b);
+  row_gather_n<V, WT, 1, SV>(P, T, w, u, k, wk, row_out, lead, val, val, &a, &b);
   return a;
 }
 
 // Phase-A gather of the interleaved {s, p}: as = sum w s[col], ap = sum w p[col]
 // (ap skipped on the first iteration, when p is not defined yet).
-template <typename V, typename V2, typename WT>
+template <typename V, typename V2, typename WT, bool SV>
 __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
                                              int k, int wk, int* row_out, bool* lead, const V2* sp, bool first, V* as,
                                              V* ap) {
-  const RowUnit g = row_unit_geom(P, T, u, k);
+  const RowUnit g = row_unit_geom<SV>(P, T, u, k);
+  const bool ws = SV && g.wt != nullptr && static_cast<int>(sizeof(WT)) == T.wbytes;
   const int row = g.r0 + wk / g.lc;
   const int lane = wk & (g.lc - 1);
   V a1 = V(0), a2 = V(0);
@@ -537,7 +580,7 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
       for (int i = 0; i < 4; ++i) {
         const int j = j0 + i * g.lc;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
-        wv[i] = j < jb ? __ldg(w + g.jbase + j) : WT(0);
+        wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
       V2 v[4];
 #pragma unroll
@@ -564,7 +607,7 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
 // Coefficient gather: acc = sum over grids l (this lane's share, l = lane,
 // lane + L, ...) of w[l][m] * val(crow[l][m]); up to 8 entries per lane are
 // staged together.
-template <typename V, typename WT, typename Val>
+template <typename V, typename WT, bool SV, typename Val>
 __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int c, int k,
                                          int wk, int* m_out, bool* lead, Val val) {
   const int L = P.coef_lanes;
@@ -573,6 +616,9 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
   const int m = c * cpc + mi;
   const int lane = wk & (L - 1);
   const int* cr = k < T.cachedB ? T.pool + T.hdrB[k] : nullptr;
+  const WT* wsm = (SV && cr && static_cast<int>(sizeof(WT)) == T.wbytes)
+                      ? reinterpret_cast<const WT*>(T.pool + wt_start(T.hdrB[k], P.K * cpc))
+                      : nullptr;
   V acc = V(0);
   if (m < P.N) {
     const int64_t N = P.N;
@@ -583,7 +629,7 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
       for (int i = 0; i < 8; ++i) {
         const int l = lb + i * L;
         idx[i] = l < P.K ? (cr ? cr[l * cpc + mi] : __ldg(P.crow + l * N + m)) : -1;
-        wv[i] = l < P.K ? __ldg(w + l * N + m) : WT(0);
+        wv[i] = l < P.K ? (wsm ? wsm[l * cpc + mi] : __ldg(w + l * N + m)) : WT(0);
       }
       V v[8];
 #pragma unroll
@@ -631,7 +677,7 @@ template <typename V> struct Vec2;
 template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
 
-template <int BT, typename V, typename WT, typename XT>
+template <int BT, typename V, typename WT, typename XT, bool SV>
 __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const WT* wcsr, const WT* wcm,
                           typename Vec2<V>::T* sp, V* q, XT* x, double gamma0, double tol, int max_iter, int stall,
                           int* iters_out, double* gamma_out, int* status_out, double* red) {
@@ -680,7 +726,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     // ================= phase A: q = A s + beta A p
     {
       auto gather_a = [&](int u, int k, V* as, V* ap, int* row, bool* lead) {
-        row_gather_sp<V, V2, WT>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
+        row_gather_sp<V, V2, WT, SV>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
       };
       int u = tm.rank;
       V as = V(0), ap = V(0);
@@ -758,7 +804,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       if (wk >= 0) {
         if (c < ncc) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
+          t = coef_gather<V, WT, SV>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
         }
       } else {
         const float dl = warp0_team_sum_f(P.pr32, nru);
@@ -783,7 +829,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       for (; c < ncc; c += tm.G, ++k) {
         if (k > 0 && wk >= 0) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
+          t = coef_gather<V, WT, SV>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
         float part = 0.0f;
         if (wk >= 0 && lead) {
@@ -1073,11 +1119,12 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
 // nonempty bins, then the FP64 solve, or FP64 normal-residual sweeps around
 // FP32 inner solves (mixed).
 // ---------------------------------------------------------------------------
-template <int BT>
+template <int BT, bool SV>
 __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned char* dsm, int smem_bytes) {
   const DevPlan& P = *J.plan;
   BlockTabs T;
-  load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T, J.precision == FCT_MIXED && P.n_w_units > 0 && P.s_init == nullptr);
+  load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T, J.precision == FCT_MIXED && P.n_w_units > 0 && P.s_init == nullptr,
+                      SV ? (J.precision == FCT_MIXED ? 4 : 8) : 0);
   const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units;
   const int wk = static_cast<int>(threadIdx.x) - 32;
   const int nce = (P.N + BT - 1) / BT;  // elementwise units over coefficients
@@ -1119,7 +1166,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       int m = 0;
       bool lead = false;
       double t = 0.0;
-      if (wk >= 0) t = coef_gather<double, double>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
+      if (wk >= 0) t = coef_gather<double, double, SV>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
       double part = 0.0;
       if (lead) {
         stcg(P.sp + m, make_double2(t, 0.0));
@@ -1138,7 +1185,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
   if (!isfinite(gamma0)) {
     status = FCT_ERR_NONFINITE;
   } else if (J.precision != FCT_MIXED) {
-    if (!cg_normal<BT, double, double, double>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, J.coeffs, gamma0, J.tol,
+    if (!cg_normal<BT, double, double, double, SV>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, J.coeffs, gamma0, J.tol,
                                                J.max_iter, 0, &iters, &gfinal, &status, red))
       return false;
   } else if (gamma0 > 0.0) {
@@ -1163,7 +1210,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       if (P.n_w_units > 0) {
         if (!pcg_normal_w<BT>(P, tm, T, g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in, &st_in))
           return false;
-      } else if (!cg_normal<BT, float, float, float>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32,
+      } else if (!cg_normal<BT, float, float, float, SV>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32,
                                                      g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in,
                                                      &st_in, red)) {
         return false;
@@ -1185,7 +1232,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         int row = 0;
         bool lead = false;
         const double ax =
-            row_gather<double, double>(P, T, P.wcsr, u, ku, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
+            row_gather<double, double, SV>(P, T, P.wcsr, u, ku, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
         if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
       }
       if (!team_sync(tm)) return false;
@@ -1195,7 +1242,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         bool lead = false;
         double t = 0.0;
         if (wk >= 0)
-          t = coef_gather<double, double>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
+          t = coef_gather<double, double, SV>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
         double part = 0.0;
         if (lead) {
           stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));
@@ -1222,7 +1269,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         int it64 = 0, st64 = FCT_OK;
         double g_out = g64;
         const double tol_eff = J.tol * sqrt(gamma0 / g64);
-        if (!cg_normal<BT, double, double, double>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, x, g64, tol_eff, J.max_iter,
+        if (!cg_normal<BT, double, double, double, SV>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, x, g64, tol_eff, J.max_iter,
                                                    0, &it64, &g_out, &st64, red))
           return false;
         iters += it64;
@@ -1271,7 +1318,7 @@ __device__ __forceinline__ void st_release_sys_i32(int* p, int v) {
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-template <int BT>
+template <int BT, bool SV>
 __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs a) {
   __shared__ double red[BT / 32 + 2];
   __shared__ int s_job;
@@ -1328,7 +1375,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
       const SolveJob J = s_jobdesc;
       __syncthreads();
       if (j < 0) break;
-      if (!solve_job<BT>(J, tm, red, dsm, a.smem_bytes)) return;
+      if (!solve_job<BT, SV>(J, tm, red, dsm, a.smem_bytes)) return;
       if (tm.rank == 0 && threadIdx.x == 0) {
         __threadfence_system();
         st_release_sys_i32(&a.ring->slots[j % kRingSize].done, 1);
@@ -1341,7 +1388,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
     return;
   }
   if (a.jobs == nullptr) {
-    if (team == 0 && solve_job<BT>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
+    if (team == 0 && solve_job<BT, SV>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
     return;
   }
   for (;;) {
@@ -1352,7 +1399,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
     const int j = s_job;
     __syncthreads();
     if (j >= a.njobs) break;
-    if (!solve_job<BT>(a.jobs[j], tm, red, dsm, a.smem_bytes)) return;
+    if (!solve_job<BT, SV>(a.jobs[j], tm, red, dsm, a.smem_bytes)) return;
   }
   team_exit(tm);
 }
@@ -1962,6 +2009,7 @@ struct fct_plan_s {
   std::vector<int32_t> ru_first, rowptr_h;  // for the shared-memory sizing of other team sizes
   std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
   int cl_smem = 0;                          // dynamic shared memory per block of the cluster solver
+  bool stage_values = false;                // single launches stage the CG loop's entry values too
   bool dirty_state = false;
 };
 
@@ -1981,21 +2029,24 @@ fct_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 template <int BT>
-const void* kernel_ptr() {
-  return reinterpret_cast<const void*>(&fct_solve_kernel<BT>);
+const void* kernel_ptr(bool stage_values) {
+  return stage_values ? reinterpret_cast<const void*>(&fct_solve_kernel<BT, true>)
+                      : reinterpret_cast<const void*>(&fct_solve_kernel<BT, false>);
 }
 
-const void* solve_kernel_for(int bt) {
+// stage_values: the variant that also stages the CG loop's entry values in
+// shared memory (single transforms whose tables fit; see choose_shape).
+const void* solve_kernel_for(int bt, bool stage_values = false) {
   switch (bt) {
-    case 128: return kernel_ptr<128>();
-    case 512: return kernel_ptr<512>();
-    default: return kernel_ptr<256>();
+    case 128: return kernel_ptr<128>(stage_values);
+    case 512: return kernel_ptr<512>(stage_values);
+    default: return kernel_ptr<256>(stage_values);
   }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_t st) {
+fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_t st, bool stage_values = false) {
   // Reset the per-launch header (queue head, error flag); team barriers are
   // self-cleaning and re-zeroed only after an abandoned launch.
   // Single-transform launches need no reset (team counters reset themselves at
@@ -2008,37 +2059,47 @@ fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_
   }
   P->dirty_state = false;
   void* kargs[] = {const_cast<SolveArgs*>(&args)};
-  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads), dim3(grid), dim3(P->block_threads), kargs,
+  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads, stage_values), dim3(grid),
+                                       dim3(P->block_threads), kargs,
                                        static_cast<size_t>(args.smem_bytes), st));
   return FCT_OK;
 }
 
 // Shared memory (bytes) a block of rank `rank` in a team of G blocks needs to
 // stage its table share (see load_block_tabs).
-size_t block_smem_need(const fct_plan P, int G, int rank) {
+size_t block_smem_need(const fct_plan P, int G, int rank, bool with_values) {
   const DevPlan& hp = P->hp;
   size_t ints = 0;
   int nA = 0, nB = 0;
+  // staged entry values: FP32 for the mixed path's inner loop, FP64 otherwise,
+  // each after its unit's indices at an 8-byte boundary (one int of padding)
+  const size_t wi = with_values ? (P->opt.precision == FCT_MIXED ? 1 : 2) : 0;
   for (int u = rank; u < hp.n_row_units; u += G, ++nA) {
     const int r0 = P->ru_first[u], r1 = P->ru_first[u + 1];
-    ints += (r1 - r0 + 1) + (P->rowptr_h[r1] - P->rowptr_h[r0]);
+    const size_t ne = static_cast<size_t>(P->rowptr_h[r1] - P->rowptr_h[r0]);
+    ints += (r1 - r0 + 1) + ne + 1 + wi * ne;
   }
-  for (int c = rank; c < hp.n_coef_chunks; c += G, ++nB) ints += static_cast<size_t>(hp.K) * hp.coefs_per_chunk;
+  for (int c = rank; c < hp.n_coef_chunks; c += G, ++nB)
+    ints += static_cast<size_t>(hp.K) * hp.coefs_per_chunk * (1 + wi) + 1;
   int nW = 0;
   if (hp.n_w_units > 0 && P->opt.precision == FCT_MIXED)
     for (int u = rank; u < hp.n_w_units; u += G, ++nW) {
       const int r0 = u * hp.w_rows_per_unit, r1 = std::min(hp.N, r0 + hp.w_rows_per_unit);
       ints += (r1 - r0 + 1) + 2 * static_cast<size_t>(P->w_rowptr_h[r1] - P->w_rowptr_h[r0]);
     }
-  ints += 5 * nA + nB + 2 * nW;
+  ints += 5 * nA + nB + 2 * nW + 1;
   return static_cast<size_t>(hp.mats_smem) * sizeof(double) + 4 * ints;
 }
 
-size_t team_smem_need(const fct_plan P, int G) {
+size_t team_smem_need(const fct_plan P, int G, bool with_values) {
   size_t need = 0;
-  for (int r = 0; r < G; ++r) need = std::max(need, block_smem_need(P, G, r));
+  for (int r = 0; r < G; ++r) need = std::max(need, block_smem_need(P, G, r, with_values));
   return need;
 }
+
+// Dynamic shared memory of a launch with teams of G blocks that stages only
+// the index tables (batches, serving, the condition probe).
+size_t launch_smem(const fct_plan P, int G, size_t cap) { return std::min(team_smem_need(P, G, false), cap); }
 
 fct_status choose_shape(fct_plan P) {
   int dev = 0;
@@ -2058,6 +2119,8 @@ fct_status choose_shape(fct_plan P) {
   cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
   cap = std::max(cap, 0) & ~15;
   FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                cap));
   P->blocks_per_sm = per_sm;
   P->smem_cap = cap;
   P->max_coresident = per_sm * prop.multiProcessorCount;
@@ -2067,11 +2130,20 @@ fct_status choose_shape(fct_plan P) {
   int g = std::min(P->max_coresident, units);
   if (P->opt.max_blocks > 0) g = std::min(g, P->opt.max_blocks);
   P->grid_blocks = std::max(g, 1);
-  P->smem_bytes = static_cast<int>(std::min<size_t>(team_smem_need(P, P->grid_blocks), cap) + 15) & ~15;
+  // A single transform on the whole GPU also stages the entry values of the
+  // CG loop when every block's share fits (fct_solve_kernel<BT, true>).
+  const size_t need_values = team_smem_need(P, P->grid_blocks, true);
+  P->stage_values = need_values <= static_cast<size_t>(cap);
+  P->smem_bytes = static_cast<int>((P->stage_values ? need_values : launch_smem(P, P->grid_blocks, cap)) + 15) & ~15;
   P->smem_bytes = std::min(P->smem_bytes, cap);
   int chk = 0;
   FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, kfn, P->block_threads, P->smem_bytes));
   if (chk * prop.multiProcessorCount < P->grid_blocks) return fail(FCT_ERR_CUDA, "solver grid does not fit");
+  if (P->stage_values) {
+    FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, solve_kernel_for(P->block_threads, true),
+                                                           P->block_threads, P->smem_bytes));
+    if (chk * prop.multiProcessorCount < P->grid_blocks) P->stage_values = false;
+  }
   return FCT_OK;
 }
 
@@ -2644,7 +2716,7 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
   a.smem_bytes = P->smem_bytes;
   const bool cluster = P->hp.cl_cs > 0 && P->opt.precision == FCT_MIXED;
   if (cluster) a.single.flags = kJobPrepareOnly;  // the team kernel forms b and A^T b
-  fct_status s = launch_solve(P, a, P->grid_blocks, st);
+  fct_status s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
   if (s != FCT_OK) return s;
   if (cluster) {
     s = launch_cluster(P, coeffs, st);
@@ -2727,7 +2799,7 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
   a.ls = P0->ls;
   a.timeout_ns = timeout_ns(P0);
   size_t need = 0;
-  for (int i = 0; i < B; ++i) need = std::max(need, team_smem_need(plans[i], G));
+  for (int i = 0; i < B; ++i) need = std::max(need, launch_smem(plans[i], G, static_cast<size_t>(P0->smem_cap)));
   a.smem_bytes = static_cast<int>(std::min<size_t>(need, P0->smem_cap) + 15) & ~15;
   a.smem_bytes = std::min(a.smem_bytes, P0->smem_cap);
   fct_status s = launch_solve(P0, a, teams * G, st);
@@ -2781,6 +2853,7 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
   C->max_coresident = src->max_coresident;
   C->blocks_per_sm = src->blocks_per_sm;
   C->smem_bytes = src->smem_bytes;
+  C->stage_values = src->stage_values;
   C->smem_cap = src->smem_cap;
   C->ru_first = src->ru_first;
   C->rowptr_h = src->rowptr_h;
