@@ -287,7 +287,10 @@ def run_gpu(args):
 
     precisions = ["fp64", "mixed"] if args.precision == "auto" else [args.precision]
     opts = {"fp64": dict(precision=F.FCT_FP64, tol=1e-13),
-            "mixed": dict(precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)}
+            # inner FP32 solves to 1e-4 relative: three FP64 sweeps then reach the
+            # 1e-12 normal residual (measured fastest of 3e-4 .. 1e-6 on this
+            # workload; the error against the oracle is checked below)
+            "mixed": dict(precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)}
     results = {}
     for prec in precisions:
         plan = F.Plan(w.support, w.sizes, w.nodes, **opts[prec])
@@ -525,7 +528,7 @@ def run_serving(args, F):
     shapes, sel = serving_workloads(args.serving_kappa0)
     t_select = time.perf_counter() - t0
     eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=args.serving_team_blocks,
-                        precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5, max_iter=20000)
+                        precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4, max_iter=20000)
     inputs, truth = {}, {}
     for s, w in enumerate(shapes):
         p = eng.plans[s]
