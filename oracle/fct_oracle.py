@@ -18,7 +18,7 @@ What it computes (Algorithm 3, Sec. 3.4): for an L-grid of K tensor grids,
 and the grid-count selection of Algorithm 2 (Sec. 3.3): grids are appended
 in a given candidate order until kappa(A) <= kappa0.
 
-Readings of the paper this oracle follows (each also listed in the design doc):
+Readings of the paper this oracle follows:
   * grid: Chebyshev extrema x_j = cos(pi j / (n-1)), j = 0..n-1, with a DCT-I
     per axis and an unsigned fold; the paper's own form (first-kind points,
     1/M DCT-II quadrature, signed half-weight alias entries, Eq.
