@@ -40,6 +40,7 @@ SERVING_REQUESTS = 200
 SERVING_KAPPA0 = 20.0
 SERVING_VARIANTS = 4         # Gaussian-cosine inputs per serving shape (plus one polynomial)
 BATCH = 38                   # batched leg: transforms of the bench workload per launch
+HETERO_BATCH = 512           # heterogeneous batch leg: transforms per launch (grid counts by Algorithm 2)
 ACCURACY_POINTS = 5000       # random points of the L-infinity error of the approximation
 
 
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--serving-team-blocks", type=int, default=38)
     ap.add_argument("--batch", type=int, default=BATCH, help="transforms per launch of the batched leg (0 = skip)")
     ap.add_argument("--batch-team-blocks", type=int, default=16)
+    ap.add_argument("--hetero-batch", type=int, default=HETERO_BATCH,
+                    help="transforms of the heterogeneous batch leg (D 3..8, degree 6..14; 0 = skip)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-budget", type=float, default=CPU_BUDGET_S, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-fraction", type=float, default=1.0, help=argparse.SUPPRESS)
@@ -343,6 +346,7 @@ def run_gpu(args):
         plan.close()
 
     batched = run_batched(args, F, w, opts["mixed"], flush) if args.batch > 0 else None
+    hetero = run_hetero_batch(args, F, opts["mixed"]) if args.hetero_batch > 0 and rank == 0 and world == 1 else None
     if batched is not None and world > 1:
         batched["total_s"] = max_over_ranks(batched["total_s"], device="cuda")
 
@@ -409,6 +413,8 @@ def run_gpu(args):
     if batched is not None:
         batched["value"] = whole_job_value(batched["coeffs_per_launch"], args.steps, world, batched["total_s"])
         line["batched"] = batched
+    if hetero is not None:
+        line["hetero_batch"] = hetero
     if serving is not None:
         line["serving"] = serving
     if cpu is not None:
@@ -486,6 +492,66 @@ def run_batched(args, F, w, opts, flush) -> dict:
             "max_iterations": max(r["iterations"] for r in reps),
             "batch_equals_alone": same, "unit": UNIT,
             "note": "independent transforms of the bench workload in one persistent launch (fct_execute_batch)"}
+
+
+def run_hetero_batch(args, F, opts) -> dict:
+    """The 512-transform heterogeneous batch (D ~ U{3..8}, total degree
+    ~ U{6..14}, polynomial plus Gaussian-cosine targets) in one persistent launch
+    per step, each transform's grid count chosen by Algorithm 2 (kappa0 = 20,
+    candidates 10 D grids) before the timed region."""
+    from concurrent.futures import ThreadPoolExecutor
+    import torch
+    import workloads as W
+    from paper_2309_14584_gb300 import lgrid
+    cands = W.config_batch(B=args.hetero_batch, grids_per_dim=10)
+
+    def select(w):
+        r = lgrid.select_grids(w.support, w.sizes, w.nodes, kappa0=SERVING_KAPPA0, start=3 * w.D,
+                               step=max(1, w.D // 2), probe_iterations=200)
+        return r["L"] if r["L"] is not None else min(r["probes"], key=lambda k: r["probes"][k] * k)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(16) as ex:   # plan building is host work; the library releases the GIL
+        Ls = list(ex.map(select, cands))
+    t_select = time.perf_counter() - t0
+    ws = [W.first_grids(w, L) for w, L in zip(cands, Ls)]
+    with ThreadPoolExecutor(16) as ex:
+        plans = list(ex.map(lambda w: F.Plan(w.support, w.sizes, w.nodes, **opts), ws))
+    xs, cs = [], []
+    for p, w in zip(plans, ws):
+        x = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(w.family, w.params, x)
+        xs.append(x)
+        cs.append(torch.empty(p.N, dtype=torch.float64, device="cuda"))
+    hs = [p.handle for p in plans]
+    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks)
+    # exact recovery of the polynomial part is not available (the target adds a
+    # Gaussian-cosine term); the smallest transform is checked against its
+    # single-launch result instead (same arithmetic: bit-identical)
+    small = min(range(len(plans)), key=lambda i: plans[i].N)
+    alone = torch.empty(plans[small].N, dtype=torch.float64, device="cuda")
+    plans[small].execute(xs[small], alone)
+    same = bool(torch.equal(alone, cs[small]))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    steps = 2
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        e0.record(stream)
+        F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks, report=False)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+    sum_n = sum(p.N for p in plans)
+    out = {"transforms_per_launch": len(plans), "value": sum_n / (ms / 1e3), "unit": UNIT, "ms_per_launch": ms,
+           "coeffs_per_launch": sum_n, "samples_per_launch": sum(p.M for p in plans), "timed_launches": steps,
+           "grid_selection_s": round(t_select, 1), "grid_count_over_3D_median": sorted(L / (3 * w.D) for L, w in zip(Ls, cands))[len(Ls) // 2],
+           "all_converged": all(r["status"] == 0 for r in reps), "max_iterations": max(r["iterations"] for r in reps),
+           "batch_equals_alone": same, "team_blocks": args.batch_team_blocks, "path": "mixed",
+           "note": "inputs larger than L2; grid counts by Algorithm 2 (kappa0 = 20) before the timed region"}
+    for p in plans:
+        p.close()
+    return out
 
 
 # ---------------------------------------------------------------------------

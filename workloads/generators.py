@@ -241,21 +241,22 @@ def binom(n: int, k: int) -> int:
     return math.comb(n, k)
 
 
-def config_batch(seed: int = 4, B: int = 512) -> list:
+def config_batch(seed: int = 4, B: int = 512, grids_per_dim: int = 3) -> list:
     """B independent transforms: D ~ U{3..8}, total degree d ~ U{6..14}, each
     target a seeded sparse polynomial on P^D_d plus the Gaussian-cosine
     function.  The nominal per-transform grid count is drawn from {4..10} and
     recorded in the name; the L-grid uses L = 3D grids with sizes {1..d+1}
     (Algorithm 1), the paper's default, because nominal counts that small
-    leave total-degree supports rank-deficient."""
+    leave total-degree supports rank-deficient.  A larger grids_per_dim
+    extends each transform's grid sequence (the candidates of Algorithm 2)."""
     g = stream(seed, "batch")
     out = []
     for t in range(B):
         D = int(g.integers(3, 9))
         d = int(g.integers(6, 15))
         k_nominal = int(g.integers(4, 11))
-        out.append(make_workload(f"b{t}_D{D}_d{d}_Knom{k_nominal}", seed * 1_000_003 + t, D, d, 3 * D, 1, d + 1,
-                                 FAMILY_POLY_GAUSSCOS, tol=1e-12, precision="mixed"))
+        out.append(make_workload(f"b{t}_D{D}_d{d}_Knom{k_nominal}", seed * 1_000_003 + t, D, d, grids_per_dim * D,
+                                 1, d + 1, FAMILY_POLY_GAUSSCOS, tol=1e-12, precision="mixed"))
     return out
 
 
