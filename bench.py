@@ -565,8 +565,9 @@ def serving_workloads(kappa0: float, probe_iterations: int = 200):
     iteration)."""
     import workloads as W
     from paper_2309_14584_gb300 import lgrid
-    shapes, sel = [], []
-    for cand in W.serving_shapes(grids_per_dim=10):
+    from concurrent.futures import ThreadPoolExecutor
+
+    def select(cand):
         t0 = time.perf_counter()
         r = lgrid.select_grids(cand.support, cand.sizes, cand.nodes, kappa0=kappa0, start=3 * cand.D,
                                step=max(1, cand.D // 2), probe_iterations=probe_iterations)
@@ -574,10 +575,12 @@ def serving_workloads(kappa0: float, probe_iterations: int = 200):
         if L is None:
             L = min(r["probes"], key=lambda k: r["probes"][k] * k)
             r["kappa"] = r["probes"][L]
-        shapes.append(W.first_grids(cand, L))
-        sel.append({"D": cand.D, "d": cand.d, "N": cand.N, "L": L, "kappa_est": r["kappa"],
-                    "probes": len(r["probes"]), "select_s": round(time.perf_counter() - t0, 3)})
-    return shapes, sel
+        return W.first_grids(cand, L), {"D": cand.D, "d": cand.d, "N": cand.N, "L": L, "kappa_est": r["kappa"],
+                                        "probes": len(r["probes"]), "select_s": round(time.perf_counter() - t0, 3)}
+
+    with ThreadPoolExecutor(8) as ex:   # plan building is host work; the library releases the GIL
+        out = list(ex.map(select, W.serving_shapes(grids_per_dim=10)))
+    return [o[0] for o in out], [o[1] for o in out]
 
 
 def run_serving(args, F):
