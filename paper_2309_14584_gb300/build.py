@@ -1,7 +1,9 @@
 """Build the in-tree CUDA library libfct_gb300.so for sm_103a with nvcc.
 
-Two translation units are compiled in parallel and linked into one shared
-library (static CUDA runtime), next to this file.  No torch headers are used:
+The translation units (host tables, the library's host code and small
+kernels, and one per block size for the team solver kernels) are compiled in
+parallel and linked into one shared library (static CUDA runtime), next to
+this file.  No torch headers are used:
 the library's ABI is plain C (include/fct.h).
 """
 from __future__ import annotations
@@ -18,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfct_gb300.so")
 
-SOURCES = ["fct_device.cu", "fct_plan_host.cpp"]
+SOURCES = ["fct_solve_k256.cu", "fct_solve_k128.cu", "fct_solve_k512.cu", "fct_device.cu", "fct_plan_host.cpp"]
+HEADERS = ["fct_internal.h", "fct_common.cuh", "fct_solver.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +34,7 @@ def nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += [os.path.join(CSRC, "fct_internal.h"), os.path.join(INCLUDE, "fct.h"), __file__]
+    files += [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "fct.h"), __file__]
     return files
 
 
@@ -47,7 +50,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # template kernel stubs get external linkage, so that host code in one
+    # translation unit can launch the solver kernels instantiated in another
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-static-global-template-stub=false",
+                     "-I", INCLUDE, "-I", CSRC]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
     procs, objs = [], []
