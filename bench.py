@@ -42,6 +42,7 @@ SERVING_VARIANTS = 4         # Gaussian-cosine inputs per serving shape (plus on
 BATCH = 38                   # batched leg: transforms of the bench workload per launch
 HETERO_BATCH = 512           # heterogeneous batch leg: transforms per launch (grid counts by Algorithm 2)
 ACCURACY_POINTS = 5000       # random points of the L-infinity error of the approximation
+SOLVER_SOURCES = ("fct_common.cuh", "fct_solver.cuh")  # hashed to match a profile to the kernel code
 
 
 def parse():
@@ -222,11 +223,14 @@ def profiled_traffic(profile_name: str):
     kernel source changed since that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", profile_name)
-    src = os.path.join(ROOT, "paper_2309_14584_gb300", "csrc", "fct_device.cu")
+    csrc = os.path.join(ROOT, "paper_2309_14584_gb300", "csrc")
     try:
         fields = dict(line.split(":", 1) for line in open(path) if ":" in line and not line.startswith(" "))
         want = fields.get("source_sha256", "").strip()
-        have = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for name in SOLVER_SOURCES:   # the team solver kernel's code
+            h.update(open(os.path.join(csrc, name), "rb").read())
+        have = h.hexdigest()
         if want and want == have:
             return int(fields["dram_bytes_per_launch"].strip())
     except Exception:
