@@ -12,11 +12,17 @@
  *   Eq. (aliasing_matrix_nd_diff)), by the CG method on the least-squares
  *   problem (CGLS).
  *
- * Grid and DCT kind implemented here: Chebyshev extrema points
- * x_j = cos(pi j/(n-1)), j = 0..n-1, with an interpolating DCT-I per axis, so
- * that degree m folds to fold_n(m) = r <= n-1 ? r : 2(n-1)-r, r = m mod 2(n-1).
+ * Grid and DCT kinds (fct_options.grid_kind):
+ *   FCT_GRID_EXTREMA (default): Chebyshev extrema points
+ *     x_j = cos(pi j/(n-1)), j = 0..n-1, with an interpolating DCT-I per axis,
+ *     so that degree m folds to fold_n(m) = r <= n-1 ? r : 2(n-1)-r,
+ *     r = m mod 2(n-1), with entry 1.
+ *   FCT_GRID_FIRST_KIND: the paper's own form, first-kind points
+ *     x_j = cos((j+1/2) pi/n) (Eq. (chebyshev_grid)), the 1/n DCT-II
+ *     quadrature of Eq. (quad_1D) and the signed entries 1, +-1/2, 0 of
+ *     Eq. (aliasing_matrix_1d).
  * An axis with n == 1 holds one sample at a caller-given node xi; a column's
- * entry on such a grid is prod_{i: n_i = 1} T_{m_i}(xi_i).
+ * entry on such a grid carries the factor prod_{i: n_i = 1} T_{m_i}(xi_i).
  *
  * Conventions for every function:
  *   - Return value: fct_status (FCT_OK == 0).  No function throws or aborts.
@@ -113,7 +119,9 @@ typedef struct {
                          says whether it does), else the team solver.  0 (default) =
                          team solver.  Batches, serving and fct_execute_noalloc use
                          the team solver.  With normal_matrix = 0 (auto), asking for
-                         the cluster solver keeps the plan from storing W.           */
+                         the cluster solver keeps the plan from storing W.  Measured
+                         on GB300 it only matches the team solver on very small plans
+                         (N ~ 150) and is 3-4x slower at N >= 1e3.                   */
 } fct_options;
 
 typedef struct {
