@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--serving-team-blocks", type=int, default=38)
     ap.add_argument("--batch", type=int, default=BATCH, help="transforms per launch of the batched leg (0 = skip)")
     ap.add_argument("--batch-team-blocks", type=int, default=16)
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="fix the launch shape (with --coef-lanes) instead of autotuning it")
+    ap.add_argument("--coef-lanes", type=int, default=0)
     ap.add_argument("--hetero-batch", type=int, default=HETERO_BATCH,
                     help="transforms of the heterogeneous batch leg (D 3..8, degree 6..14; 0 = skip)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
@@ -299,6 +302,20 @@ def run_gpu(args):
             # workload; the error against the oracle is checked below)
             "mixed": dict(precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)}
     results = {}
+    from paper_2309_14584_gb300.tune import autotune
+    probe_plan = F.Plan(w.support, w.sizes, w.nodes)
+    probe_plan.sample(w.family, w.params, samples)   # the samples do not depend on the launch shape
+    probe_plan.close()
+    tuned = {}
+    base_opts = {p: dict(o) for p, o in opts.items()}   # the batch legs keep the default launch shape
+    for prec in precisions:
+        if args.block_threads:
+            fixed = dict(opts[prec], block_threads=args.block_threads, coef_lanes=args.coef_lanes)
+            tuned[prec] = {"options": fixed, "ms": None, "timings": []}
+        else:
+            # launch shape picked by timing a few candidates (outside the timed region)
+            tuned[prec] = autotune(w.support, w.sizes, w.nodes, samples, opts[prec])
+        opts[prec] = tuned[prec]["options"]
     for prec in precisions:
         plan = F.Plan(w.support, w.sizes, w.nodes, **opts[prec])
         plan.sample(w.family, w.params, samples)
@@ -342,15 +359,15 @@ def run_gpu(args):
         for _ in range(e2e_n):
             plan.execute_host(s_host, c_host)
         e2e_s = (time.perf_counter() - t0) / e2e_n
-        results[prec] = dict(plan_info=plan.info, rep=rep, rep_last=rep_last, coeffs=c_first,
+        results[prec] = dict(plan_info=plan.info, rep=rep, rep_last=rep_last, coeffs=c_first, tuning=tuned[prec],
                              step_ms=step_ms, total_s=total_s, t_wall=t_wall, clocks=clk, deterministic=same,
                              e2e_s=e2e_s, e2e_host_equal=bool(np.array_equal(c_host.numpy(), c_first)))
         if prec == "mixed":
             results[prec]["accuracy"] = approximation_error(F, plan, w, torch.from_numpy(c_first).cuda())
         plan.close()
 
-    batched = run_batched(args, F, w, opts["mixed"], flush) if args.batch > 0 else None
-    hetero = run_hetero_batch(args, F, opts["mixed"]) if args.hetero_batch > 0 and rank == 0 and world == 1 else None
+    batched = run_batched(args, F, w, base_opts["mixed"], flush) if args.batch > 0 else None
+    hetero = run_hetero_batch(args, F, base_opts["mixed"]) if args.hetero_batch > 0 and rank == 0 and world == 1 else None
     if batched is not None and world > 1:
         batched["total_s"] = max_over_ranks(batched["total_s"], device="cuda")
 
@@ -396,7 +413,10 @@ def run_gpu(args):
         "config": dict(workload_config(w), path=best, iterations=R0["rep"]["iterations"],
                        refinements=R0["rep"]["refinements"], nonempty_bins=info["R"],
                        solver_blocks=info["grid_blocks"], block_threads=info["block_threads"],
-                       coef_lanes=info["coef_lanes"], parallelism=f"replicas x{world}"),
+                       coef_lanes=info["coef_lanes"], parallelism=f"replicas x{world}",
+                       launch_tuning={"chosen": {k: v for k, v in R0["tuning"]["options"].items()
+                                                 if k in ("block_threads", "coef_lanes", "entries_per_lane")},
+                                      "candidates_ms": [[c, round(ms, 4)] for c, ms in R0["tuning"]["timings"]]}),
         "rel_err_vs_oracle": R0["rel_err"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"],
