@@ -1,0 +1,30 @@
+"""The launch-shape autotuner picks one of its candidates, and the plan built
+with the chosen shape still meets the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2309_14584_gb300 as F
+import workloads as W
+from oracle import fct_oracle as O
+from paper_2309_14584_gb300.tune import CANDIDATES, autotune
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_choice_solves_to_tolerance():
+    w = W.make_workload("tune", 43, 4, 5, 12, 1, 6, W.FAMILY_GAUSSCOS)
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes)
+    ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+    x = torch.from_numpy(f).cuda()
+    opts = dict(precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)
+    r = autotune(w.support, w.sizes, w.nodes, x, opts, reps=3)
+    assert len(r["timings"]) == len(CANDIDATES) and r["ms"] > 0
+    chosen = {k: v for k, v in r["options"].items() if k not in opts}
+    assert chosen in [dict(c) for c in CANDIDATES]
+    plan = F.Plan(w.support, w.sizes, w.nodes, **r["options"])
+    c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    rep = plan.execute(x, c)
+    plan.close()
+    assert rep["status"] == 0
+    assert np.linalg.norm(c.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
