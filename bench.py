@@ -432,6 +432,17 @@ def run_gpu(args):
                           "rel_err_vs_oracle": r["rel_err"], "deterministic": r["deterministic"],
                           "e2e_value": w.N / r["e2e_s"]} for p, r in results.items()},
     }
+    # synchronisation floor of the chosen launch shape: two team barriers per CG iteration
+    try:
+        us_bar = F.fct_measure_team_barrier(info["grid_blocks"], info["block_threads"], 2000)
+        line["sync_floor"] = {"us_per_team_barrier": us_bar, "blocks": info["grid_blocks"],
+                              "block_threads": info["block_threads"], "barriers_per_cg_iteration": 2,
+                              "us_per_step_per_cg_iteration": 1e3 * statistics.mean(R0["step_ms"]) /
+                              max(1, R0["rep"]["iterations"]),
+                              "note": "empty-phase barrier crossings (fct_measure_team_barrier) vs the "
+                                      "step time divided by its CG iterations (DCT and sweeps included)"}
+    except Exception as e:  # measurement only; the bench line stands without it
+        line["sync_floor"] = {"error": str(e)[:200]}
     if "accuracy" in results.get("mixed", {}):
         line["accuracy"] = results["mixed"]["accuracy"]
     if batched is not None:

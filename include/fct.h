@@ -331,6 +331,16 @@ fct_status fct_plan_condition(fct_plan plan, const double* start, double* work, 
 fct_status fct_evaluate(fct_plan plan, const double* coeffs, int64_t npoints, const double* points, double* values,
                         void* stream);
 
+/*
+ * Measurement utility (no counterpart in the paper): time `rounds` crossings of
+ * the library's team barrier by `blocks` co-resident blocks of block_threads
+ * threads (128, 256 or 512) with no work in between; *us_per_barrier =
+ * elapsed / rounds.  A CG iteration of the team solver crosses two barriers,
+ * so this is the synchronisation floor of an iteration.  Every wait is
+ * bounded (4 s).  Synchronous; allocates and frees its own small state.
+ */
+fct_status fct_measure_team_barrier(int blocks, int block_threads, int rounds, double* us_per_barrier);
+
 /* Release a plan's device memory (synchronises the device first). NULL is OK. */
 fct_status fct_destroy(fct_plan plan);
 

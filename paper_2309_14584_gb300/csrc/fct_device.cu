@@ -1724,6 +1724,60 @@ extern "C" fct_status fct_selftest_wait_timeout(double timeout_s, int* status_ou
 }
 
 // ---------------------------------------------------------------------------
+// Synchronisation floor: the team barrier alone, `rounds` times over `blocks`
+// co-resident blocks (no work between barriers), so that a transform's time
+// per CG iteration can be set against two barrier crossings.
+// ---------------------------------------------------------------------------
+__global__ void barrier_probe_kernel(LaunchState* ls, int rounds, unsigned long long timeout_ns) {
+  Team tm;
+  tm.G = static_cast<int>(gridDim.x);
+  tm.rank = static_cast<int>(blockIdx.x);
+  tm.epoch = 0;
+  tm.bar = &ls->bars[0];
+  tm.err = &ls->err;
+  tm.timeout_ns = timeout_ns;
+  for (int r = 0; r < rounds; ++r)
+    if (!team_sync(tm)) return;
+  team_exit(tm);
+}
+
+extern "C" fct_status fct_measure_team_barrier(int blocks, int block_threads, int rounds, double* us_per_barrier) {
+  if (!us_per_barrier || rounds < 1 || rounds > 1000000 || blocks < 1 ||
+      (block_threads != 128 && block_threads != 256 && block_threads != 512))
+    return fail(FCT_ERR_INVALID_ARG, "need blocks >= 1, block_threads 128/256/512, rounds in [1, 1e6]");
+  int dev = 0, nsm = 0, per_sm = 0;
+  FCT_CUDA(cudaGetDevice(&dev));
+  FCT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_probe_kernel, block_threads, 0));
+  if (blocks > per_sm * nsm) return fail(FCT_ERR_INVALID_ARG, "more blocks than can be co-resident");
+  LaunchState* ls = nullptr;
+  FCT_CUDA(cudaMalloc(&ls, sizeof(LaunchState)));
+  cudaError_t e = cudaMemset(ls, 0, sizeof(LaunchState));
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  unsigned long long tns = 4000000000ull;
+  void* kargs[] = {&ls, &rounds, &tns};
+  if (e == cudaSuccess) e = cudaEventRecord(a);
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(barrier_probe_kernel), dim3(blocks),
+                                    dim3(block_threads), kargs, 0, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(b);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int err = 0;
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaMemcpy(&err, &ls->err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(ls);
+  if (e != cudaSuccess) return cuda_fail(e, "team barrier probe");
+  if (err != 0) return fail(static_cast<fct_status>(err), "team barrier probe: a wait expired");
+  *us_per_barrier = 1e3 * static_cast<double>(ms) / rounds;
+  return FCT_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Serving (continuous batching): a persistent launch whose teams take jobs
 // from a ring in host-mapped memory as they are published; a job submitted
 // while others run is picked up by the next team that frees up.  When no job

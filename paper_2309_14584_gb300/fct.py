@@ -115,6 +115,8 @@ SIGNATURES = [
     ("fct_destroy", ctypes.c_int, [_P]),
     ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
     ("fct_evaluate", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    ("fct_measure_team_barrier", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double)]),
     ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int), _P]),
@@ -318,6 +320,13 @@ def fct_evaluate(plan: int, coeffs, points, values, stream=None):
     """values[p] = sum_m coeffs[m] prod_i T_{m_i}(points[p, i]) (device buffers)."""
     n = int(points.shape[0]) if hasattr(points, "shape") else 0
     _check(lib().fct_evaluate(plan, _ptr(coeffs), n, _ptr(points), _ptr(values), _stream(stream)))
+
+
+def fct_measure_team_barrier(blocks: int, block_threads: int = 256, rounds: int = 2000) -> float:
+    """Microseconds per crossing of the team barrier with no work in between."""
+    us = ctypes.c_double()
+    _check(lib().fct_measure_team_barrier(blocks, block_threads, rounds, ctypes.byref(us)))
+    return us.value
 
 
 def fct_plan_clone(plan: int) -> int:

@@ -28,3 +28,18 @@ def test_autotune_choice_solves_to_tolerance():
     plan.close()
     assert rep["status"] == 0
     assert np.linalg.norm(c.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("blocks,bt", [(1, 256), (8, 256), (152, 512), (304, 256)])
+def test_team_barrier_floor_is_measured(blocks, bt):
+    us = F.fct_measure_team_barrier(blocks, bt, 500)
+    assert 0.0 < us < 100.0
+
+
+def test_team_barrier_probe_rejects_bad_arguments():
+    with pytest.raises(F.FctError):
+        F.fct_measure_team_barrier(0, 256, 10)
+    with pytest.raises(F.FctError):
+        F.fct_measure_team_barrier(100000, 256, 10)
+    with pytest.raises(F.FctError):
+        F.fct_measure_team_barrier(4, 96, 10)
