@@ -287,6 +287,17 @@ fct_status fct_server_poll(fct_server server, int64_t ticket, int* done, fct_rep
 fct_status fct_server_wait(fct_server server, int64_t ticket, double timeout_s, fct_report* rep);
 fct_status fct_server_destroy(fct_server server);
 
+/*
+ * The right-hand side alone (the first stage of fct_execute): every grid's
+ * DCT of the samples (device double[M]), evaluated at the nonempty bins,
+ * Eq. (main_linear_system)'s b = F f with the rows of empty bins dropped.
+ *   b:    device double[R], in the plan's internal row order;
+ *   bins: host int64[R] or NULL: for every row, the sample index of its bin
+ *         (grid offset + row-major bin index), which identifies the row.
+ * For checks of the DCT stage against a reference.  Synchronous.
+ */
+fct_status fct_plan_rhs(fct_plan plan, const double* samples, double* b, int64_t* bins, void* stream);
+
 /* Report of the plan's last execute (waits for stream). */
 fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);
 

@@ -638,6 +638,7 @@ struct fct_plan_s {
   std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
   int cl_smem = 0;                          // dynamic shared memory per block of the cluster solver
   bool stage_values = false;                // single launches stage the CG loop's entry values too
+  double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
 };
 
@@ -1354,6 +1355,38 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
   return FCT_OK;
 }
 
+fct_status fct_plan_rhs(fct_plan P, const double* samples, double* b, int64_t* bins, void* stream) {
+  if (!P || !samples || !b) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the team kernel's first stage only: DCT passes, b at the nonempty bins, s = A^T b
+  SolveArgs a{};
+  a.single = make_job(P, samples, P->d_stage_rhs_x ? P->d_stage_rhs_x : nullptr, P->drep);
+  if (!P->d_stage_rhs_x) {
+    FCT_CUDA(cudaMalloc(&P->d_stage_rhs_x, sizeof(double) * P->N));
+    a.single.coeffs = P->d_stage_rhs_x;
+  }
+  a.single.flags = kJobPrepareOnly;
+  a.jobs = nullptr;
+  a.njobs = 1;
+  a.team_blocks = P->grid_blocks;
+  a.ls = P->ls;
+  a.timeout_ns = timeout_ns(P);
+  a.smem_bytes = P->smem_bytes;
+  fct_status s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
+  if (s != FCT_OK) return s;
+  FCT_CUDA(cudaMemcpyAsync(b, P->hp.b, sizeof(double) * P->R, cudaMemcpyDeviceToDevice, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
+  int err = 0;
+  FCT_CUDA(cudaMemcpy(&err, &P->ls->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err != 0) {
+    P->dirty_state = true;
+    return fail(static_cast<fct_status>(err), "fct_plan_rhs: device-side error");
+  }
+  if (bins)
+    for (int64_t r = 0; r < P->R; ++r) bins[r] = P->H.rowsrc[r];
+  return FCT_OK;
+}
+
 fct_status fct_plan_last_report(fct_plan P, void* stream, fct_report* rep) {
   if (!P || !rep) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
   return read_report(P, P->drep, static_cast<cudaStream_t>(stream), rep);
@@ -1444,6 +1477,7 @@ fct_status fct_destroy(fct_plan P) {
   if (P->d_stage_out) cudaFree(P->d_stage_out);
   if (P->djobs) cudaFree(P->djobs);
   if (P->d_hist_block) cudaFree(P->d_hist_block);
+  if (P->d_stage_rhs_x) cudaFree(P->d_stage_rhs_x);
   if (P->wmem) cudaFree(P->wmem);
   P->tables.reset();  // frees the table allocation with its last user
   delete P;

@@ -115,6 +115,7 @@ SIGNATURES = [
     ("fct_destroy", ctypes.c_int, [_P]),
     ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
     ("fct_evaluate", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
+    ("fct_plan_rhs", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("fct_measure_team_barrier", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double)]),
     ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -327,6 +328,15 @@ def fct_measure_team_barrier(blocks: int, block_threads: int = 256, rounds: int 
     us = ctypes.c_double()
     _check(lib().fct_measure_team_barrier(blocks, block_threads, rounds, ctypes.byref(us)))
     return us.value
+
+
+def fct_plan_rhs(plan: int, samples, b, stream=None) -> np.ndarray:
+    """b = F f at the nonempty bins into the device buffer b (double[R]);
+    returns each row's sample index (host int64[R])."""
+    R = fct_plan_get_info(plan)["R"]
+    bins = np.zeros(R, dtype=np.int64)
+    _check(lib().fct_plan_rhs(plan, _ptr(samples), _ptr(b), _ptr(bins), _stream(stream)))
+    return bins
 
 
 def fct_plan_clone(plan: int) -> int:

@@ -324,3 +324,28 @@ def test_bounded_wait_times_out_and_context_survives():
     w = W.config_small_poly()
     got, _, rep = gpu_run(w, tol=1e-13)
     assert rep["status"] == 0 and rel(got, w.coeffs_true) <= TOL_FP64
+
+
+RHS_CASES = SMALL[:4] + [("D6_d10", None, None, None, None, None, None, None)]
+
+
+@pytest.mark.parametrize("case", RHS_CASES, ids=[c[0] for c in RHS_CASES])
+@pytest.mark.parametrize("kind", ["extrema", "first"])
+def test_rhs_dct_stage_matches_oracle(case, kind):
+    """The DCT stage alone (fct_plan_rhs): b = F f at the nonempty bins equals
+    the oracle's per-grid DCT (direct matrix products) row by row, and the
+    rows are exactly the oracle's nonempty bins."""
+    w = W.config_d6_gausscos() if case[1] is None else _small(case)
+    gk = F.FCT_GRID_EXTREMA if kind == "extrema" else F.FCT_GRID_FIRST_KIND
+    f = O.sample_lgrid(w.family, w.params, w.support, w.sizes, w.nodes, kind=kind)
+    s = O.AliasSystem(w.support, w.sizes, w.nodes, kind=kind)
+    ref = s.rhs(f)
+    plan = F.Plan(w.support, w.sizes, w.nodes, grid_kind=gk)
+    b = torch.empty(plan.info["R"], dtype=torch.float64, device="cuda")
+    bins = F.fct_plan_rhs(plan.handle, torch.from_numpy(f).cuda(), b)
+    plan.close()
+    order = np.argsort(bins, kind="stable")
+    want_bins = np.concatenate([s.offsets[l] + s.rows[l] for l in range(len(s.rows))])
+    assert np.array_equal(bins[order], want_bins)
+    got = b.cpu().numpy()[order]
+    assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(f)))
