@@ -288,6 +288,17 @@ fct_status fct_server_wait(fct_server server, int64_t ticket, double timeout_s, 
 fct_status fct_server_destroy(fct_server server);
 
 /*
+ * The alias operator alone (Eq. (L-grid_A_mat) with the rows of empty bins
+ * dropped), from the plan's device tables in FP64:
+ *   transpose = 0: out[R] = A in[N]   (rows in the plan's internal order);
+ *   transpose = 1: out[N] = A^T in[R] (in[] in the internal row order).
+ * in / out: device doubles; bins: host int64[R] or NULL, each row's sample
+ * index (grid offset + row-major bin index).  For checks against a
+ * reference.  Asynchronous on stream.
+ */
+fct_status fct_plan_apply(fct_plan plan, const double* in, double* out, int transpose, int64_t* bins, void* stream);
+
+/*
  * The right-hand side alone (the first stage of fct_execute): every grid's
  * DCT of the samples (device double[M]), evaluated at the nonempty bins,
  * Eq. (main_linear_system)'s b = F f with the rows of empty bins dropped.

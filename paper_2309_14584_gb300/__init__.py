@@ -7,6 +7,6 @@ from .fct import (FCT_FAMILY_GAUSSCOS, FCT_FAMILY_POLY, FCT_FAMILY_POLY_GAUSSCOS
                   FCT_GRID_FIRST_KIND,
                   FCT_FAMILY_RATIONAL, FCT_FP64, FCT_MIXED, FctError, Plan, fct_alias_tables_host,
                   fct_default_options, fct_destroy, fct_evaluate, fct_measure_team_barrier, fct_execute, fct_execute_batch, fct_execute_host, fct_execute_noalloc,
-                  fct_grid_offsets, fct_plan_clone, fct_plan_condition, fct_plan_rhs, fct_plan_create, fct_server_create, fct_server_destroy,
+                  fct_grid_offsets, fct_plan_clone, fct_plan_condition, fct_plan_rhs, fct_plan_apply, fct_plan_create, fct_server_create, fct_server_destroy,
                   fct_server_poll, fct_server_submit, fct_server_wait, fct_plan_get_info, fct_plan_last_report, fct_sample,
                   lib, library_path)

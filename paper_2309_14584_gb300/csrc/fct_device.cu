@@ -532,6 +532,32 @@ __global__ void eval_pass_kernel(const DevPlan* __restrict__ Pp, const DctChunk*
 }
 
 // ---------------------------------------------------------------------------
+// The alias operator on its own (fct_plan_apply): y = A x over the bin-major
+// CSR (one thread per row, entries in CSR order) and x = A^T y over the
+// coefficient-major table (one thread per coefficient, grids in order), the
+// same tables and FP64 entries the solver uses.
+// ---------------------------------------------------------------------------
+__global__ void alias_apply_kernel(const DevPlan* __restrict__ Pp, const double* __restrict__ in,
+                                   double* __restrict__ out, int transpose) {
+  const DevPlan& P = *Pp;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (!transpose) {
+    if (i >= P.R) return;
+    double acc = 0.0;
+    for (int j = P.rowptr[i]; j < P.rowptr[i + 1]; ++j) acc = fma(P.wcsr[j], in[P.col[j]], acc);
+    out[i] = acc;
+  } else {
+    if (i >= P.N) return;
+    double acc = 0.0;
+    for (int l = 0; l < P.K; ++l) {
+      const int64_t e = static_cast<int64_t>(l) * P.N + i;
+      acc = fma(P.wcm[e], in[P.crow[e]], acc);
+    }
+    out[i] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Evaluation of the expansion p(x) = sum_m c_m prod_i T_{m_i}(x_i) at
 // arbitrary points (how the paper measures approximation error).  One warp
 // per point: its lanes build the point's T_k(x_i) tables (three-term
@@ -1352,6 +1378,19 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
     if (s != FCT_OK) return s;
   }
   if (rep) return read_report(P, P->drep, st, rep);
+  return FCT_OK;
+}
+
+fct_status fct_plan_apply(fct_plan P, const double* in, double* out, int transpose, int64_t* bins, void* stream) {
+  if (!P || !in || !out) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  const int64_t n = transpose ? P->N : P->R;
+  if (n > 0) {
+    alias_apply_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        P->dp, in, out, transpose ? 1 : 0);
+    FCT_CUDA(cudaGetLastError());
+  }
+  if (bins)
+    for (int64_t r = 0; r < P->R; ++r) bins[r] = P->H.rowsrc[r];
   return FCT_OK;
 }
 

@@ -116,6 +116,7 @@ SIGNATURES = [
     ("fct_plan_clone", ctypes.c_int, [ctypes.POINTER(_P), _P]),
     ("fct_evaluate", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     ("fct_plan_rhs", ctypes.c_int, [_P, _P, _P, _P, _P]),
+    ("fct_plan_apply", ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
     ("fct_measure_team_barrier", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double)]),
     ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -328,6 +329,15 @@ def fct_measure_team_barrier(blocks: int, block_threads: int = 256, rounds: int 
     us = ctypes.c_double()
     _check(lib().fct_measure_team_barrier(blocks, block_threads, rounds, ctypes.byref(us)))
     return us.value
+
+
+def fct_plan_apply(plan: int, x, y, transpose: bool = False, stream=None) -> np.ndarray:
+    """y = A x (transpose False) or y = A^T x (True) on device buffers; returns
+    each row's sample index (host int64[R])."""
+    R = fct_plan_get_info(plan)["R"]
+    bins = np.zeros(R, dtype=np.int64)
+    _check(lib().fct_plan_apply(plan, _ptr(x), _ptr(y), 1 if transpose else 0, _ptr(bins), _stream(stream)))
+    return bins
 
 
 def fct_plan_rhs(plan: int, samples, b, stream=None) -> np.ndarray:

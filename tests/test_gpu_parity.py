@@ -349,3 +349,30 @@ def test_rhs_dct_stage_matches_oracle(case, kind):
     assert np.array_equal(bins[order], want_bins)
     got = b.cpu().numpy()[order]
     assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(f)))
+
+
+@pytest.mark.parametrize("case", RHS_CASES, ids=[c[0] for c in RHS_CASES])
+@pytest.mark.parametrize("kind", ["extrema", "first"])
+def test_alias_operator_matches_oracle(case, kind):
+    """A x and A^T y from the plan's device tables (fct_plan_apply) equal the
+    oracle's fold-built sparse matrix products, row by row."""
+    w = W.config_d6_gausscos() if case[1] is None else _small(case)
+    gk = F.FCT_GRID_EXTREMA if kind == "extrema" else F.FCT_GRID_FIRST_KIND
+    s = O.AliasSystem(w.support, w.sizes, w.nodes, kind=kind)
+    g = W.stream(31, "probe")
+    x = g.standard_normal(w.N)
+    y = g.standard_normal(s.R)
+    plan = F.Plan(w.support, w.sizes, w.nodes, grid_kind=gk)
+    ax = torch.empty(s.R, dtype=torch.float64, device="cuda")
+    bins = F.fct_plan_apply(plan.handle, torch.from_numpy(x).cuda(), ax)
+    order = np.argsort(bins, kind="stable")          # internal row order -> oracle order
+    y_int = np.empty(s.R)
+    y_int[order] = y                                  # y in the plan's internal row order
+    aty = torch.empty(w.N, dtype=torch.float64, device="cuda")
+    F.fct_plan_apply(plan.handle, torch.from_numpy(y_int).cuda(), aty, transpose=True)
+    torch.cuda.synchronize()
+    plan.close()
+    ref_ax = s.A @ x
+    ref_aty = s.A.T @ y
+    assert np.max(np.abs(ax.cpu().numpy()[order] - ref_ax)) <= 1e-13 * max(1.0, np.abs(ref_ax).max())
+    assert np.max(np.abs(aty.cpu().numpy() - ref_aty)) <= 1e-13 * max(1.0, np.abs(ref_aty).max())
