@@ -445,6 +445,10 @@ def run_gpu(args):
         line["sync_floor"] = {"error": str(e)[:200]}
     if "accuracy" in results.get("mixed", {}):
         line["accuracy"] = results["mixed"]["accuracy"]
+    try:
+        line["plan_build"] = plan_build_times(F, w)
+    except Exception as e:  # measurement only; the bench line stands without it
+        line["plan_build"] = {"error": str(e)[:200]}
     if batched is not None:
         batched["value"] = whole_job_value(batched["coeffs_per_launch"], args.steps, world, batched["total_s"])
         line["batched"] = batched
@@ -465,8 +469,32 @@ def run_gpu(args):
 
 
 # ---------------------------------------------------------------------------
-# batched leg and approximation error
+# plan construction, batched leg and approximation error
 # ---------------------------------------------------------------------------
+def plan_build_times(F, w, reps=3) -> dict:
+    """Wall time of fct_plan_create (validation, tables, DCT set-up, upload and
+    workspace allocation) with the alias tables built in host C++ and on the
+    device, median of `reps` after one untimed build each, on the bench
+    workload and on D=10 degree 8."""
+    import workloads as W
+    out = {}
+    for name, wl in (("D6_d10", w), ("D10_d8", W.config_d10_rational())):
+        row = {"K_N": int(wl.K * wl.N)}
+        for key, pb in (("host_ms", F.FCT_PLAN_BUILD_HOST), ("device_ms", F.FCT_PLAN_BUILD_DEVICE)):
+            ts = []
+            for i in range(reps + 1):
+                t0 = time.perf_counter()
+                p = F.Plan(wl.support, wl.sizes, wl.nodes, precision=F.FCT_MIXED, plan_build=pb)
+                dt = 1e3 * (time.perf_counter() - t0)
+                p.close()
+                if i > 0:
+                    ts.append(dt)
+            row[key] = round(statistics.median(ts), 3)
+        row["speedup"] = round(row["host_ms"] / row["device_ms"], 2)
+        out[name] = row
+    return out
+
+
 def approximation_error(F, plan, w, coeffs_dev) -> dict:
     """L-infinity error of the computed expansion against the target at random
     points of [-1, 1]^D (the paper's accuracy measure), evaluated on the

@@ -122,7 +122,17 @@ typedef struct {
                          the cluster solver keeps the plan from storing W.  Measured
                          on GB300 it only matches the team solver on very small plans
                          (N ~ 150) and is 3-4x slower at N >= 1e3.                   */
+  int plan_build;     /* where fct_plan_create builds the alias tables: FCT_PLAN_BUILD_AUTO
+                         (0, default) and FCT_PLAN_BUILD_DEVICE (2) on the GPU (fold,
+                         stable radix sort by bin, compaction, row order: kernels),
+                         FCT_PLAN_BUILD_HOST (1) in host C++.  Both give the same
+                         tables bit for bit (fct_plan_tables).  The device build
+                         needs transient scratch of about 110 bytes per entry (K N). */
 } fct_options;
+
+#define FCT_PLAN_BUILD_AUTO 0
+#define FCT_PLAN_BUILD_HOST 1
+#define FCT_PLAN_BUILD_DEVICE 2
 
 typedef struct {
   int status;                 /* fct_status of this transform                        */
@@ -308,6 +318,20 @@ fct_status fct_plan_apply(fct_plan plan, const double* in, double* out, int tran
  * For checks of the DCT stage against a reference.  Synchronous.
  */
 fct_status fct_plan_rhs(fct_plan plan, const double* samples, double* b, int64_t* bins, void* stream);
+
+/*
+ * The plan's alias tables, copied from the device into host buffers (any
+ * pointer may be NULL to skip that table), rows in the plan's internal order:
+ *   rowptr int32[R+1], col int32[K N], wcsr double[K N]: A's rows as CSR
+ *     (one row per nonempty bin, columns ascending inside a row);
+ *   crow int32[K N], wcm double[K N]: coefficient-major, [K][N], the row and
+ *     value of column m's entry on grid l at l N + m;
+ *   bins int64[R]: each row's sample index (grid offset + row-major bin).
+ * For checking table builds against each other and against a reference.
+ * Synchronous.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_CUDA.
+ */
+fct_status fct_plan_tables(fct_plan plan, int32_t* rowptr, int32_t* col, double* wcsr, int32_t* crow, double* wcm,
+                           int64_t* bins);
 
 /* Report of the plan's last execute (waits for stream). */
 fct_status fct_plan_last_report(fct_plan plan, void* stream, fct_report* rep);

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfct_gb300.so")
 
-SOURCES = ["fct_solve_k256.cu", "fct_solve_k128.cu", "fct_solve_k512.cu", "fct_device.cu", "fct_plan_host.cpp"]
+SOURCES = ["fct_solve_k256.cu", "fct_solve_k128.cu", "fct_solve_k512.cu", "fct_device.cu", "fct_plan_device.cu",
+           "fct_plan_host.cpp"]
 HEADERS = ["fct_internal.h", "fct_common.cuh", "fct_solver.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -52,8 +53,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cc = nvcc()
     # template kernel stubs get external linkage, so that host code in one
     # translation unit can launch the solver kernels instantiated in another
-    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-static-global-template-stub=false",
-                     "-I", INCLUDE, "-I", CSRC]
+    # host code rounds every floating-point operation on its own (no fused
+    # multiply-add), so host- and device-built tables agree bit for bit on
+    # x86 and Arm hosts alike
+    common = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+                     "-static-global-template-stub=false", "-I", INCLUDE, "-I", CSRC]
     if ptxas_info:
         common += ["-Xptxas", "-v"]
     procs, objs = [], []

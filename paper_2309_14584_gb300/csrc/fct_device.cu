@@ -948,10 +948,13 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   cudaError_t ce = cudaGetDeviceCount(&ndev);
   if (ce != cudaSuccess || ndev < 1) return fail(FCT_ERR_NO_DEVICE, "no CUDA device");
 
+  if (o.plan_build < 0 || o.plan_build > 2) return fail(FCT_ERR_INVALID_ARG, "plan_build must be 0, 1 or 2");
+  const bool on_device = o.plan_build != FCT_PLAN_BUILD_HOST;
+
   auto* P = new fct_plan_s();
   P->opt = o;
   std::string err;
-  fct_status s = build_host_tables(D, N, support, K, sizes, nodes, o.grid_kind, true, &P->H, &err);
+  fct_status s = build_host_tables(D, N, support, K, sizes, nodes, o.grid_kind, true, &P->H, &err, !on_device);
   if (s != FCT_OK) {
     delete P;
     return fail(s, err);
@@ -961,7 +964,6 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   P->K = K;
   P->N = N;
   P->M = H.M;
-  P->R = H.R;
   P->sizes.assign(sizes, sizes + static_cast<size_t>(K) * D);
   for (int64_t e = 0; e < N * D; ++e) P->dmax = std::max<int>(P->dmax, support[e]);
   P->block_threads = o.block_threads;
@@ -977,6 +979,32 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     L = 1;
     while (L < 16 && L * 8 < K) L <<= 1;
   }
+  // Entries per gather lane: the smallest of 2, 4, 8 whose row units fit in
+  // one wave of co-resident blocks (a block with two units while others have
+  // one makes everybody wait at the next barrier).
+  int epl = 8;
+  int64_t wave = 0;  // co-resident blocks of the solver kernel
+  {
+    int per_sm = 0, nsm = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(BT), BT, 0) == cudaSuccess)
+      wave = static_cast<int64_t>(per_sm) * nsm;
+  }
+  DeviceTables DT;  // device-built tables (scratch, freed on return)
+  if (on_device) {
+    s = build_device_tables(&H, support, sizes, nodes, o.grid_kind, workers, wave, o.entries_per_lane, &epl, &DT);
+    if (s != FCT_OK) {
+      delete P;
+      return s;
+    }
+  } else {
+    int64_t classes[3][6];
+    lane_class_counts(H, classes);
+    epl = pick_entries_per_lane(classes, workers, wave, o.entries_per_lane);
+    device_row_order(&H, epl);
+  }
+  P->R = H.R;
   DevPlan& hp = P->hp;
   hp.N = static_cast<int32_t>(N);
   hp.R = static_cast<int32_t>(H.R);
@@ -989,26 +1017,6 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.coefs_per_chunk = workers / L;
   hp.n_coef_chunks = static_cast<int32_t>((N + hp.coefs_per_chunk - 1) / hp.coefs_per_chunk);
   hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
-  // Entries per gather lane: the smallest of 2, 4, 8 whose row units fit in
-  // one wave of co-resident blocks (a block with two units while others have
-  // one makes everybody wait at the next barrier).
-  int epl = 8;
-  int64_t wave = 0;  // co-resident blocks of the solver kernel
-  {
-    int per_sm = 0, nsm = 0, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, solve_kernel_for(BT), BT, 0) == cudaSuccess) {
-      wave = static_cast<int64_t>(per_sm) * nsm;
-      for (int e : {2, 4, 8})
-        if (count_row_units(H, workers, e) <= wave) {
-          epl = e;
-          break;
-        }
-      if (o.entries_per_lane > 0) epl = o.entries_per_lane;
-    }
-  }
-  device_row_order(&H, epl);
   std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
   row_units(H, workers, epl, &ru_first, &ru_lanes);
   final_pass_rows(H, &rowbase, &rowk);
@@ -1030,6 +1038,13 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     if (o.normal_matrix > 0 && bound > (int64_t{1} << 30)) {
       delete P;
       return fail(FCT_ERR_INVALID_ARG, "normal_matrix = 1 but A^T A would exceed 2^30 nonzeros");
+    }
+    if (want && N > 0 && on_device) {
+      s = download_device_tables(DT, &H);
+      if (s != FCT_OK) {
+        delete P;
+        return s;
+      }
     }
     if (want && N > 0) {
       std::vector<double> wv64;
@@ -1158,14 +1173,18 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.wcol = d_wcol;
   hp.wval = d_wval;
 
-  std::vector<float> w32(KN), wc32(KN);
-  for (int64_t i = 0; i < KN; ++i) {
-    w32[i] = static_cast<float>(H.wcsr[i]);
-    wc32[i] = static_cast<float>(H.weight[i]);
+  std::vector<float> w32, wc32;
+  if (!on_device) {
+    w32.resize(KN);
+    wc32.resize(KN);
+    for (int64_t i = 0; i < KN; ++i) {
+      w32[i] = static_cast<float>(H.wcsr[i]);
+      wc32[i] = static_cast<float>(H.weight[i]);
+    }
   }
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
-    return cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    return cudaMemcpy(dst, src, bytes, on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice);
   };
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) {
@@ -1182,13 +1201,15 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(d_ru_first, ru_first.data(), sizeof(int32_t) * ru_first.size()));
   chk(up(d_ru_lanes, ru_lanes.data(), sizeof(int32_t) * ru_lanes.size()));
   chk(up(d_rowptr, H.rowptr.data(), sizeof(int32_t) * (H.R + 1)));
-  chk(up(d_col, H.col.data(), sizeof(int32_t) * KN));
-  chk(up(d_wcsr, H.wcsr.data(), sizeof(double) * KN));
-  chk(up(d_wcsr32, w32.data(), sizeof(float) * KN));
-  // coefficient-major row table holds global rows
-  chk(up(d_crow, H.crow.data(), sizeof(int32_t) * KN));
-  chk(up(d_wcm, H.weight.data(), sizeof(double) * KN));
-  chk(up(d_wcm32, wc32.data(), sizeof(float) * KN));
+  // alias tables (the coefficient-major row table holds global rows): from
+  // the device build's scratch, or from the host tables
+  chk(up(d_col, on_device ? static_cast<const void*>(DT.col) : H.col.data(), sizeof(int32_t) * KN));
+  chk(up(d_wcsr, on_device ? static_cast<const void*>(DT.wcsr) : H.wcsr.data(), sizeof(double) * KN));
+  chk(up(d_wcsr32, on_device ? static_cast<const void*>(DT.wcsr32) : w32.data(), sizeof(float) * KN));
+  chk(up(d_crow, on_device ? static_cast<const void*>(DT.crow) : H.crow.data(), sizeof(int32_t) * KN));
+  chk(up(d_wcm, on_device ? static_cast<const void*>(DT.wcm) : H.weight.data(), sizeof(double) * KN));
+  chk(up(d_wcm32, on_device ? static_cast<const void*>(DT.wcm32) : wc32.data(), sizeof(float) * KN));
+  DT.release();
   if (nnzw > 0) {
     chk(up(d_wrowptr, w_rowptr.data(), sizeof(int32_t) * (N + 1)));
     chk(up(d_wcol, w_col.data(), sizeof(int32_t) * nnzw));
@@ -1224,6 +1245,25 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   H.weight.clear(); H.weight.shrink_to_fit();
   H.crow.clear(); H.crow.shrink_to_fit();
   *out = P;
+  return FCT_OK;
+}
+
+fct_status fct_plan_tables(fct_plan P, int32_t* rowptr, int32_t* col, double* wcsr, int32_t* crow, double* wcm,
+                           int64_t* bins) {
+  if (!P) return fail(FCT_ERR_INVALID_ARG, "NULL plan");
+  const int64_t KN = static_cast<int64_t>(P->K) * P->N, R = P->R;
+  cudaError_t ue = cudaSuccess;
+  auto down = [&](void* dst, const void* src, size_t bytes) {
+    if (dst && ue == cudaSuccess) ue = cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost);
+  };
+  down(rowptr, P->hp.rowptr, sizeof(int32_t) * (R + 1));
+  down(col, P->hp.col, sizeof(int32_t) * KN);
+  down(wcsr, P->hp.wcsr, sizeof(double) * KN);
+  down(crow, P->hp.crow, sizeof(int32_t) * KN);
+  down(wcm, P->hp.wcm, sizeof(double) * KN);
+  if (ue != cudaSuccess) return cuda_fail(ue, "fct_plan_tables");
+  if (bins)
+    for (int64_t r = 0; r < R; ++r) bins[r] = P->H.rowsrc[r];
   return FCT_OK;
 }
 

@@ -211,9 +211,45 @@ struct HostTables {
 
 // Validates inputs and builds all host tables.  Returns FCT_OK or an error with
 // the message in *err.
+// with_alias = false leaves the alias tables (bin, crow, weight, CSR, rows)
+// empty for build_device_tables to fill.
 fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
                              const int32_t* sizes, const double* nodes, int grid_kind, bool with_dct,
-                             HostTables* out, std::string* err);
+                             HostTables* out, std::string* err, bool with_alias = true);
+
+// Alias tables built on the device (fct_plan_device.cu), already in the
+// device row order: the same arrays, bit for bit, as build_host_tables +
+// device_row_order.  All pointers live in one scratch allocation.
+struct DeviceTables {
+  void* mem = nullptr;
+  int32_t* rowptr = nullptr;   // [R+1]
+  int32_t* rowgrid = nullptr;  // [R]
+  int32_t* col = nullptr;      // [K N] bin-major
+  double* wcsr = nullptr;
+  float* wcsr32 = nullptr;
+  int32_t* crow = nullptr;     // [K N] coefficient-major
+  double* wcm = nullptr;
+  float* wcm32 = nullptr;
+  void release();
+  ~DeviceTables() { release(); }
+};
+
+// Builds the alias tables of H's plan on the current device (H holds the
+// offsets, D, K, N from build_host_tables(with_alias = false)).  Chooses the
+// entries per lane as the host path does (pick_entries_per_lane) and fills
+// H->R, H->rowptr, H->rowsrc and H->rowgrid in the device row order.
+fct_status build_device_tables(HostTables* H, const uint16_t* support, const int32_t* sizes, const double* nodes,
+                               int grid_kind, int workers, int64_t wave, int fixed_epl, int* epl,
+                               DeviceTables* out);
+// Copies col, wcsr, crow and the coefficient-major values back into H.
+fct_status download_device_tables(const DeviceTables& T, HostTables* H);
+
+// Rows per lane class: classes[q][c] counts the rows with 2^c gather lanes at
+// 2 << q entries per lane.  The entries per lane of a plan: `fixed` if > 0,
+// else the fewest of 2, 4, 8 whose row units fit in `wave` blocks, else 8.
+void lane_class_counts(const HostTables& H, int64_t classes[3][6]);
+int64_t units_from_classes(const int64_t* per_class, int workers);
+int pick_entries_per_lane(const int64_t classes[3][6], int workers, int64_t wave, int fixed);
 
 // Gather lanes of a row with len entries: min(32, pow2 >= ceil(len / epl)),
 // epl = target entries per lane.
@@ -227,7 +263,6 @@ void device_row_order(HostTables* H, int epl);
 
 // A p gather units for `workers` threads per block: a unit holds
 // workers / lanes consecutive rows of equal lane count.
-int64_t count_row_units(const HostTables& H, int workers, int epl);
 void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* first, std::vector<int32_t>* lanes);
 
 // W = A^T A (N x N, CSR, columns ascending, FP64 sums in a fixed order) and

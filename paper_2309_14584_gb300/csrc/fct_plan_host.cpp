@@ -83,7 +83,7 @@ static inline int64_t fold_first_kind(int64_t m, int64_t n, double* val) {
 
 fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
                              const int32_t* sizes, const double* nodes, int grid_kind, bool with_dct,
-                             HostTables* out, std::string* err) {
+                             HostTables* out, std::string* err, bool with_alias) {
   auto bad = [&](const std::string& m) {
     *err = m;
     return FCT_ERR_INVALID_ARG;
@@ -123,84 +123,86 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
   H.M = H.offsets[K];
 
   const int64_t KN = static_cast<int64_t>(K) * N;
-  H.bin.resize(KN);
-  H.crow.resize(KN);
-  H.weight.resize(KN);
-  H.col.resize(KN);
-  H.wcsr.resize(KN);
-  H.row_off.assign(K + 1, 0);
-  H.rowptr.clear();
-  H.rowsrc.clear();
-  H.rowgrid.clear();
-  H.rowptr.push_back(0);
+  if (with_alias) {
+    H.bin.resize(KN);
+    H.crow.resize(KN);
+    H.weight.resize(KN);
+    H.col.resize(KN);
+    H.wcsr.resize(KN);
+    H.row_off.assign(K + 1, 0);
+    H.rowptr.clear();
+    H.rowsrc.clear();
+    H.rowgrid.clear();
+    H.rowptr.push_back(0);
 
-  // Nonzero components of every multi-index (axis order): a zero component
-  // folds to bin index 0 with entry 1 on every axis kind, so only nonzero
-  // components change a bin or an entry (sparse supports in high D have few).
-  std::vector<int64_t> nz_off(N + 1, 0);
-  std::vector<int32_t> nz_axis;
-  for (int64_t m = 0; m < N; ++m) {
-    for (int i = 0; i < D; ++i)
-      if (support[m * D + i] != 0) nz_axis.push_back(i);
-    nz_off[m + 1] = static_cast<int64_t>(nz_axis.size());
-  }
-  std::vector<int64_t> stride(D);
-  std::vector<int32_t> count;
-  std::vector<int32_t> comp;
-  for (int l = 0; l < K; ++l) {
-    const int32_t* sz = sizes + static_cast<int64_t>(l) * D;
-    stride[D - 1] = 1;
-    for (int i = D - 2; i >= 0; --i) stride[i] = stride[i + 1] * sz[i + 1];
-    const int64_t T = H.offsets[l + 1] - H.offsets[l];
-    int32_t* bl = H.bin.data() + static_cast<int64_t>(l) * N;
-    double* wl = H.weight.data() + static_cast<int64_t>(l) * N;
+    // Nonzero components of every multi-index (axis order): a zero component
+    // folds to bin index 0 with entry 1 on every axis kind, so only nonzero
+    // components change a bin or an entry (sparse supports in high D have few).
+    std::vector<int64_t> nz_off(N + 1, 0);
+    std::vector<int32_t> nz_axis;
     for (int64_t m = 0; m < N; ++m) {
-      const uint16_t* mi = support + m * D;
-      int64_t bidx = 0;
-      double w = 1.0;
-      for (int64_t e = nz_off[m]; e < nz_off[m + 1]; ++e) {
-        const int i = nz_axis[e];
-        const int32_t n = sz[i];
-        if (n >= 2 && first) {
-          double v = 0.0;
-          bidx += fold_first_kind(mi[i], n, &v) * stride[i];
-          w *= v;
-        } else if (n >= 2) {
-          bidx += fold_index(mi[i], n) * stride[i];
-        } else {
-          const double xi = nodes ? nodes[l * D + i] : 1.0;
-          w *= cheb_T(mi[i], xi);
+      for (int i = 0; i < D; ++i)
+        if (support[m * D + i] != 0) nz_axis.push_back(i);
+      nz_off[m + 1] = static_cast<int64_t>(nz_axis.size());
+    }
+    std::vector<int64_t> stride(D);
+    std::vector<int32_t> count;
+    std::vector<int32_t> comp;
+    for (int l = 0; l < K; ++l) {
+      const int32_t* sz = sizes + static_cast<int64_t>(l) * D;
+      stride[D - 1] = 1;
+      for (int i = D - 2; i >= 0; --i) stride[i] = stride[i + 1] * sz[i + 1];
+      const int64_t T = H.offsets[l + 1] - H.offsets[l];
+      int32_t* bl = H.bin.data() + static_cast<int64_t>(l) * N;
+      double* wl = H.weight.data() + static_cast<int64_t>(l) * N;
+      for (int64_t m = 0; m < N; ++m) {
+        const uint16_t* mi = support + m * D;
+        int64_t bidx = 0;
+        double w = 1.0;
+        for (int64_t e = nz_off[m]; e < nz_off[m + 1]; ++e) {
+          const int i = nz_axis[e];
+          const int32_t n = sz[i];
+          if (n >= 2 && first) {
+            double v = 0.0;
+            bidx += fold_first_kind(mi[i], n, &v) * stride[i];
+            w *= v;
+          } else if (n >= 2) {
+            bidx += fold_index(mi[i], n) * stride[i];
+          } else {
+            const double xi = nodes ? nodes[l * D + i] : 1.0;
+            w *= cheb_T(mi[i], xi);
+          }
+        }
+        bl[m] = static_cast<int32_t>(bidx);
+        wl[m] = w;
+      }
+      // counting sort by bin (stable in m): nonempty bins in ascending order
+      count.assign(static_cast<size_t>(T) + 1, 0);
+      for (int64_t m = 0; m < N; ++m) count[bl[m] + 1]++;
+      comp.assign(static_cast<size_t>(T), -1);
+      const int32_t row0 = static_cast<int32_t>(H.rowsrc.size());
+      int32_t nrows = 0;
+      for (int64_t t = 0; t < T; ++t) {
+        if (count[t + 1] > 0) {
+          comp[t] = row0 + nrows++;
+          H.rowsrc.push_back(static_cast<int32_t>(H.offsets[l] + t));
+          H.rowgrid.push_back(l);
+          H.rowptr.push_back(H.rowptr.back() + count[t + 1]);
         }
       }
-      bl[m] = static_cast<int32_t>(bidx);
-      wl[m] = w;
-    }
-    // counting sort by bin (stable in m): nonempty bins in ascending order
-    count.assign(static_cast<size_t>(T) + 1, 0);
-    for (int64_t m = 0; m < N; ++m) count[bl[m] + 1]++;
-    comp.assign(static_cast<size_t>(T), -1);
-    const int32_t row0 = static_cast<int32_t>(H.rowsrc.size());
-    int32_t nrows = 0;
-    for (int64_t t = 0; t < T; ++t) {
-      if (count[t + 1] > 0) {
-        comp[t] = row0 + nrows++;
-        H.rowsrc.push_back(static_cast<int32_t>(H.offsets[l] + t));
-        H.rowgrid.push_back(l);
-        H.rowptr.push_back(H.rowptr.back() + count[t + 1]);
+      // scatter columns into CSR, m ascending within each bin
+      std::vector<int32_t> fill(nrows, 0);
+      for (int64_t m = 0; m < N; ++m) {
+        const int32_t r = comp[bl[m]];
+        H.crow[static_cast<int64_t>(l) * N + m] = r;
+        const int32_t pos = H.rowptr[r] + fill[r - row0]++;
+        H.col[pos] = static_cast<int32_t>(m);
+        H.wcsr[pos] = wl[m];
       }
+      H.row_off[l + 1] = row0 + nrows;
     }
-    // scatter columns into CSR, m ascending within each bin
-    std::vector<int32_t> fill(nrows, 0);
-    for (int64_t m = 0; m < N; ++m) {
-      const int32_t r = comp[bl[m]];
-      H.crow[static_cast<int64_t>(l) * N + m] = r;
-      const int32_t pos = H.rowptr[r] + fill[r - row0]++;
-      H.col[pos] = static_cast<int32_t>(m);
-      H.wcsr[pos] = wl[m];
-    }
-    H.row_off[l + 1] = row0 + nrows;
-  }
-  H.R = static_cast<int64_t>(H.rowsrc.size());
+    H.R = static_cast<int64_t>(H.rowsrc.size());
+  }  // with_alias
 
   // node positions of every grid axis (used by the sampler)
   H.node_off.resize(static_cast<size_t>(K) * D);
@@ -414,19 +416,31 @@ int lanes_for(int32_t len, int epl) {
   return lanes;
 }
 
-int64_t count_row_units(const HostTables& H, int workers, int epl) {
-  // rows sorted or not, the unit count only depends on the rows per lane class
-  int64_t per_class[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t r = 0; r < H.R; ++r) {
-    const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r], epl);
-    per_class[__builtin_ctz(static_cast<unsigned>(lc))]++;
-  }
+int64_t units_from_classes(const int64_t* per_class, int workers) {
   int64_t units = 0;
   for (int c = 0; c < 6; ++c) {
     const int64_t per = workers >> c;
     units += (per_class[c] + per - 1) / per;
   }
   return units;
+}
+
+int pick_entries_per_lane(const int64_t classes[3][6], int workers, int64_t wave, int fixed) {
+  if (fixed > 0) return fixed;
+  if (wave > 0)
+    for (int q = 0; q < 3; ++q)
+      if (units_from_classes(classes[q], workers) <= wave) return 2 << q;
+  return 8;
+}
+
+void lane_class_counts(const HostTables& H, int64_t classes[3][6]) {
+  // rows sorted or not, the unit count only depends on the rows per lane class
+  for (int q = 0; q < 3; ++q)
+    for (int c = 0; c < 6; ++c) classes[q][c] = 0;
+  for (int64_t r = 0; r < H.R; ++r) {
+    const int32_t len = H.rowptr[r + 1] - H.rowptr[r];
+    for (int q = 0; q < 3; ++q) classes[q][__builtin_ctz(static_cast<unsigned>(lanes_for(len, 2 << q)))]++;
+  }
 }
 
 void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* first, std::vector<int32_t>* lanes) {
@@ -543,6 +557,7 @@ void fct_default_options(fct_options* opt) {
   opt->grid_kind = FCT_GRID_EXTREMA;
   opt->entries_per_lane = 0;
   opt->cluster_solve = 0;
+  opt->plan_build = FCT_PLAN_BUILD_AUTO;
 }
 
 fct_status fct_alias_tables_host(int D, int64_t N, const uint16_t* support, int K,

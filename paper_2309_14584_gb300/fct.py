@@ -27,6 +27,9 @@ FCT_FP64 = 0
 FCT_MIXED = 1
 FCT_GRID_EXTREMA = 0
 FCT_GRID_FIRST_KIND = 1
+FCT_PLAN_BUILD_AUTO = 0
+FCT_PLAN_BUILD_HOST = 1
+FCT_PLAN_BUILD_DEVICE = 2
 
 FCT_FAMILY_POLY = 0
 FCT_FAMILY_GAUSSCOS = 1
@@ -50,6 +53,7 @@ class fct_options(ctypes.Structure):
         ("grid_kind", ctypes.c_int),
         ("entries_per_lane", ctypes.c_int),
         ("cluster_solve", ctypes.c_int),
+        ("plan_build", ctypes.c_int),
     ]
 
 
@@ -117,6 +121,7 @@ SIGNATURES = [
     ("fct_evaluate", ctypes.c_int, [_P, _P, ctypes.c_int64, _P, _P, _P]),
     ("fct_plan_rhs", ctypes.c_int, [_P, _P, _P, _P, _P]),
     ("fct_plan_apply", ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P]),
+    ("fct_plan_tables", ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     ("fct_measure_team_barrier", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double)]),
     ("fct_plan_condition", ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -338,6 +343,19 @@ def fct_plan_apply(plan: int, x, y, transpose: bool = False, stream=None) -> np.
     bins = np.zeros(R, dtype=np.int64)
     _check(lib().fct_plan_apply(plan, _ptr(x), _ptr(y), 1 if transpose else 0, _ptr(bins), _stream(stream)))
     return bins
+
+
+def fct_plan_tables(plan: int) -> dict:
+    """The plan's alias tables copied to the host (rows in the internal
+    order): rowptr int32[R+1], col int32[K N], wcsr f64[K N] (CSR), crow
+    int32[K, N], wcm f64[K, N] (coefficient-major), bins int64[R]."""
+    info = fct_plan_get_info(plan)
+    R, K, N = info["R"], info["K"], info["N"]
+    t = {"rowptr": np.zeros(R + 1, np.int32), "col": np.zeros(K * N, np.int32), "wcsr": np.zeros(K * N),
+         "crow": np.zeros((K, N), np.int32), "wcm": np.zeros((K, N)), "bins": np.zeros(R, np.int64)}
+    _check(lib().fct_plan_tables(plan, _ptr(t["rowptr"]), _ptr(t["col"]), _ptr(t["wcsr"]), _ptr(t["crow"]),
+                                 _ptr(t["wcm"]), _ptr(t["bins"])))
+    return t
 
 
 def fct_plan_rhs(plan: int, samples, b, stream=None) -> np.ndarray:
