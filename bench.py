@@ -42,6 +42,7 @@ SERVING_VARIANTS = 4         # Gaussian-cosine inputs per serving shape (plus on
 BATCH = 38                   # batched leg: transforms of the bench workload per launch
 HETERO_BATCH = 512           # heterogeneous batch leg: transforms per launch (grid counts by Algorithm 2)
 ACCURACY_POINTS = 5000       # random points of the L-infinity error of the approximation
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 rate (nominal): the ceiling of the FP64-ALU-bound evaluation kernel
 SOLVER_SOURCES = ("fct_common.cuh", "fct_solver.cuh")  # hashed to match a profile to the kernel code
 
 
@@ -372,6 +373,12 @@ def run_gpu(args):
         batched["total_s"] = max_over_ranks(batched["total_s"], device="cuda")
 
     serving = run_serving(args, F) if rank == 0 and world == 1 else None
+    next_rows = None
+    if rank == 0 and world == 1 and "mixed" in results:
+        try:
+            next_rows = run_next_rows(F, w, opts["mixed"], results["mixed"]["coeffs"], flush)
+        except Exception as e:  # measurement only; the bench line stands without it
+            next_rows = {"error": str(e)[:200]}
 
     # CPU oracle: baseline timing + reference coefficients (rank 0, N = 1 only)
     cpu = None
@@ -449,6 +456,8 @@ def run_gpu(args):
         line["plan_build"] = plan_build_times(F, w)
     except Exception as e:  # measurement only; the bench line stands without it
         line["plan_build"] = {"error": str(e)[:200]}
+    if next_rows is not None:
+        line["next_rows"] = next_rows
     if batched is not None:
         batched["value"] = whole_job_value(batched["coeffs_per_launch"], args.steps, world, batched["total_s"])
         line["batched"] = batched
@@ -511,6 +520,79 @@ def approximation_error(F, plan, w, coeffs_dev) -> dict:
     err = np.abs(vals.cpu().numpy() - f)
     return {"linf_abs_error": float(err.max()), "points": ACCURACY_POINTS,
             "note": "max |p(x) - f(x)| of the mixed-path expansion at uniform random points"}
+
+
+def _timed(fn, steps, flush):
+    """Device time of fn() per call: L2 flushed before each call, one pair of
+    CUDA events around each call on the current stream; mean in ms."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
+
+
+def run_next_rows(F, w, opts, coeffs_np, flush, steps=20) -> dict:
+    """The rows past the hot path, timed on the same GPU: the paper's
+    first-kind grid on the bench workload, evaluation of the expansion at
+    random points, and a sparse S^inf support at D = 100."""
+    import numpy as np
+    import torch
+    import workloads as W
+    out = {}
+    # first-kind grid (1/n DCT-II quadrature, signed alias entries), same workload and options
+    p = F.Plan(w.support, w.sizes, w.nodes, grid_kind=F.FCT_GRID_FIRST_KIND, **opts)
+    x = torch.empty(p.M, dtype=torch.float64, device="cuda")
+    p.sample(w.family, w.params, x)
+    c = torch.empty(p.N, dtype=torch.float64, device="cuda")
+    rep = p.execute(x, c)
+    ms = _timed(lambda: p.execute(x, c, report=False), steps, flush)
+    acc = approximation_error(F, p, w, c)
+    out["first_kind"] = {"ms_per_transform": ms, "value": w.N / (ms / 1e3), "unit": UNIT, "status": rep["status"],
+                         "iterations": rep["iterations"], "refinements": rep["refinements"],
+                         "linf_abs_error": acc["linf_abs_error"], "nonempty_bins": p.info["R"]}
+    # evaluation of the bench expansion (extrema grid coefficients) at random points
+    pe = F.Plan(w.support, w.sizes, w.nodes, **opts)
+    npts = 1 << 17
+    pts = torch.from_numpy(W.stream(23, "probe").uniform(-1.0, 1.0, (npts, w.D))).cuda()
+    vals = torch.empty(npts, dtype=torch.float64, device="cuda")
+    cd = torch.from_numpy(np.ascontiguousarray(coeffs_np)).cuda()
+    ms = _timed(lambda: pe.evaluate(cd, pts, vals), max(3, steps // 4), flush)
+    flops = npts * w.N * (w.D + 1)   # per point and term: D table products and one add, FP64
+    out["evaluate"] = {"points": npts, "terms": w.N, "ms": ms, "points_per_s": npts / (ms / 1e3),
+                       "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                                    "peak": FP64_NOMINAL_TFLOPS, "frac": flops / (ms / 1e3) / 1e12 / FP64_NOMINAL_TFLOPS,
+                                    "peak_kind": "nominal GB300 FP64"}}
+    pe.close()
+    p.close()
+    # sparse S^inf support at D = 100 (3 nonzero components per index), 10 D grids,
+    # a polynomial on the support recovered (the check that holds at any size)
+    D, d, N = 100, 9, 20_000
+    sup = W.sparse_infinity_support(13, D, d, N, 3)
+    sizes, nodes = W.l_grid(300, N, D, 10 * D, 1, d + 1)
+    c_true = W.poly_coefficients(10, sup)
+    t0 = time.perf_counter()
+    ps = F.Plan(sup, sizes, nodes, **opts)
+    t_build = time.perf_counter() - t0
+    xs = torch.empty(ps.M, dtype=torch.float64, device="cuda")
+    ps.sample(W.FAMILY_POLY | F.fct.FCT_SAMPLE_FOLDED, c_true, xs)
+    cs = torch.empty(N, dtype=torch.float64, device="cuda")
+    rep = ps.execute(xs, cs)
+    err = float(np.linalg.norm(cs.cpu().numpy() - c_true) / np.linalg.norm(c_true))
+    ms = _timed(lambda: ps.execute(xs, cs, report=False), max(3, steps // 4), flush)
+    out["sparse_D100"] = {"N": N, "K": int(sizes.shape[0]), "M": int(ps.M), "nonempty_bins": ps.info["R"],
+                          "plan_build_ms": 1e3 * t_build, "ms_per_transform": ms, "value": N / (ms / 1e3),
+                          "unit": UNIT, "status": rep["status"], "iterations": rep["iterations"],
+                          "refinements": rep["refinements"], "recovery_rel_err": err}
+    ps.close()
+    return out
 
 
 def run_batched(args, F, w, opts, flush) -> dict:

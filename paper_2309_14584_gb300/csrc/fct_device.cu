@@ -999,7 +999,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
       return s;
     }
   } else {
-    int64_t classes[3][6];
+    int64_t classes[3][kLaneClasses];
     lane_class_counts(H, classes);
     epl = pick_entries_per_lane(classes, workers, wave, o.entries_per_lane);
     device_row_order(&H, epl);

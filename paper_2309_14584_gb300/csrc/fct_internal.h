@@ -17,6 +17,13 @@ constexpr int kMaxD = 255;
 constexpr int kDctChunk = 1024;        // elements of one grid per DCT work unit
 constexpr int kMaxTeams = 1024;        // teams per launch (batched execute)
 constexpr int kMaxAxis = 4096;         // longest grid axis (points) the direct DCT-I accepts
+// Gather lane classes of a row: 1, 2, 4, 8, 16, 32 lanes, or kWideLanes: a row
+// longer than kWideRowFactor * 32 lanes * (entries per lane) is gathered by
+// every gather warp of a block (one row per unit), the warps' partial sums
+// added in warp order.
+constexpr int kWideLanes = 64;
+constexpr int kWideRowFactor = 4;
+constexpr int kLaneClasses = 7;
 
 // One DCT-I work unit: a contiguous element range of one grid tensor in one
 // axis pass.  Output element e (within the grid) is
@@ -244,15 +251,16 @@ fct_status build_device_tables(HostTables* H, const uint16_t* support, const int
 // Copies col, wcsr, crow and the coefficient-major values back into H.
 fct_status download_device_tables(const DeviceTables& T, HostTables* H);
 
-// Rows per lane class: classes[q][c] counts the rows with 2^c gather lanes at
-// 2 << q entries per lane.  The entries per lane of a plan: `fixed` if > 0,
+// Rows per lane class: classes[q][c] counts the rows with 2^c gather lanes
+// (c = 6: wide rows) at 2 << q entries per lane.  The entries per lane of a plan: `fixed` if > 0,
 // else the fewest of 2, 4, 8 whose row units fit in `wave` blocks, else 8.
-void lane_class_counts(const HostTables& H, int64_t classes[3][6]);
+void lane_class_counts(const HostTables& H, int64_t classes[3][kLaneClasses]);
 int64_t units_from_classes(const int64_t* per_class, int workers);
-int pick_entries_per_lane(const int64_t classes[3][6], int workers, int64_t wave, int fixed);
+int pick_entries_per_lane(const int64_t classes[3][kLaneClasses], int workers, int64_t wave, int fixed);
 
 // Gather lanes of a row with len entries: min(32, pow2 >= ceil(len / epl)),
-// epl = target entries per lane.
+// epl = target entries per lane; kWideLanes for rows longer than
+// kWideRowFactor * 32 * epl.
 int lanes_for(int32_t len, int epl);
 
 // Renumber the rows of H for the device: stable sort by descending gather

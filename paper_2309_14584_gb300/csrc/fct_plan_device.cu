@@ -18,7 +18,7 @@
 //      row table are permuted to it.
 // Everything between the upload of the support and the download of the row
 // pointers runs on the device; the host only chooses the entries per lane
-// from an 18-counter histogram.
+// from a 21-counter histogram.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -60,6 +60,7 @@ __device__ double cheb_T_rn(int m, double x) {
 __device__ __forceinline__ int lanes_for_dev(int32_t len, int epl) {
   int lanes = 1;
   while (lanes < 32 && lanes * epl < len) lanes <<= 1;
+  if (len > kWideRowFactor * 32 * epl) return kWideLanes;
   return lanes;
 }
 
@@ -304,28 +305,29 @@ __global__ void csr_fill_kernel(const int32_t* __restrict__ skey, const int32_t*
   }
 }
 
-// 4. lane classes.  hist[q][c]: rows whose gather lane count is 2^c with
-// 2 << q entries per lane (q = 0, 1, 2).
+// 4. lane classes.  hist[q][c]: rows whose gather lane count is 2^c (c = 6:
+// wide rows) with 2 << q entries per lane (q = 0, 1, 2).
+constexpr int kClassCounters = 3 * kLaneClasses;
 __global__ void lane_class_kernel(const int32_t* __restrict__ rowptr, int64_t R, int32_t* __restrict__ hist) {
-  __shared__ int32_t h[18];
-  if (threadIdx.x < 18) h[threadIdx.x] = 0;
+  __shared__ int32_t h[kClassCounters];
+  if (threadIdx.x < kClassCounters) h[threadIdx.x] = 0;
   __syncthreads();
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < R;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int32_t len = rowptr[r + 1] - rowptr[r];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) atomicAdd(&h[q * 6 + (__ffs(lanes_for_dev(len, 2 << q)) - 1)], 1);
+    for (int q = 0; q < 3; ++q) atomicAdd(&h[q * kLaneClasses + (__ffs(lanes_for_dev(len, 2 << q)) - 1)], 1);
   }
   __syncthreads();
-  if (threadIdx.x < 18) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
+  if (threadIdx.x < kClassCounters) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
 
-// Row sort key: 5 - log2(lanes), so rows with 32 lanes come first.
+// Row sort key: 6 - log2(lanes), so wide rows come first, then 32 lanes, ...
 __global__ void row_class_key_kernel(const int32_t* __restrict__ rowptr, int64_t R, int epl,
                                      int32_t* __restrict__ key, int32_t* __restrict__ val) {
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < R;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    key[r] = 5 - (__ffs(lanes_for_dev(rowptr[r + 1] - rowptr[r], epl)) - 1);
+    key[r] = (kLaneClasses - 1) - (__ffs(lanes_for_dev(rowptr[r + 1] - rowptr[r], epl)) - 1);
     val[r] = static_cast<int32_t>(r);
   }
 }
@@ -536,15 +538,15 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   // entries per lane from the lane-class histogram
   chk(cudaMemset(d_small, 0, sizeof(int32_t) * 32));
   lane_class_kernel<<<elem_blocks(R), kElemThreads>>>(d_rowptr0, R, d_small);
-  int32_t hist[18];
+  int32_t hist[kClassCounters];
   chk(cudaMemcpy(hist, d_small, sizeof(hist), cudaMemcpyDeviceToHost));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build (lane classes)");
   }
-  int64_t classes[3][6];
+  int64_t classes[3][kLaneClasses];
   for (int q = 0; q < 3; ++q)
-    for (int c = 0; c < 6; ++c) classes[q][c] = hist[q * 6 + c];
+    for (int c = 0; c < kLaneClasses; ++c) classes[q][c] = hist[q * kLaneClasses + c];
   const int epl = pick_entries_per_lane(classes, workers, wave, fixed_epl);
   *epl_out = epl;
 

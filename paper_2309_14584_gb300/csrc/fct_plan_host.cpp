@@ -413,19 +413,23 @@ void device_row_order(HostTables* Hp, int epl) {
 int lanes_for(int32_t len, int epl) {
   int lanes = 1;
   while (lanes < 32 && lanes * epl < len) lanes <<= 1;
+  if (len > kWideRowFactor * 32 * epl) return kWideLanes;
   return lanes;
 }
 
+// rows of one unit: workers / lanes, one for a wide row
+static inline int rows_per_unit(int lanes, int workers) { return lanes > 32 ? 1 : workers / lanes; }
+
 int64_t units_from_classes(const int64_t* per_class, int workers) {
   int64_t units = 0;
-  for (int c = 0; c < 6; ++c) {
-    const int64_t per = workers >> c;
+  for (int c = 0; c < kLaneClasses; ++c) {
+    const int64_t per = rows_per_unit(1 << c, workers);
     units += (per_class[c] + per - 1) / per;
   }
   return units;
 }
 
-int pick_entries_per_lane(const int64_t classes[3][6], int workers, int64_t wave, int fixed) {
+int pick_entries_per_lane(const int64_t classes[3][kLaneClasses], int workers, int64_t wave, int fixed) {
   if (fixed > 0) return fixed;
   if (wave > 0)
     for (int q = 0; q < 3; ++q)
@@ -433,10 +437,10 @@ int pick_entries_per_lane(const int64_t classes[3][6], int workers, int64_t wave
   return 8;
 }
 
-void lane_class_counts(const HostTables& H, int64_t classes[3][6]) {
+void lane_class_counts(const HostTables& H, int64_t classes[3][kLaneClasses]) {
   // rows sorted or not, the unit count only depends on the rows per lane class
   for (int q = 0; q < 3; ++q)
-    for (int c = 0; c < 6; ++c) classes[q][c] = 0;
+    for (int c = 0; c < kLaneClasses; ++c) classes[q][c] = 0;
   for (int64_t r = 0; r < H.R; ++r) {
     const int32_t len = H.rowptr[r + 1] - H.rowptr[r];
     for (int q = 0; q < 3; ++q) classes[q][__builtin_ctz(static_cast<unsigned>(lanes_for(len, 2 << q)))]++;
@@ -449,7 +453,7 @@ void row_units(const HostTables& H, int workers, int epl, std::vector<int32_t>* 
   int64_t r = 0;
   while (r < H.R) {
     const int lc = lanes_for(H.rowptr[r + 1] - H.rowptr[r], epl);
-    const int per = workers / lc;
+    const int per = rows_per_unit(lc, workers);
     int64_t e = r;
     // rows are sorted by lane class, so equal lane counts are contiguous
     while (e < H.R && e - r < per && lanes_for(H.rowptr[e + 1] - H.rowptr[e], epl) == lc) ++e;

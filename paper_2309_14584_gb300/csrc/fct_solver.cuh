@@ -243,8 +243,12 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
                                             V* out2) {
   const RowUnit g = row_unit_geom<SV>(P, T, u, k);
   const bool ws = SV && g.wt != nullptr && static_cast<int>(sizeof(WT)) == T.wbytes;
-  const int row = g.r0 + wk / g.lc;
-  const int lane = wk & (g.lc - 1);
+  // a wide unit is one row gathered by every gather thread of the block: each
+  // warp returns its partial sum (lead on its lane 0) for wide_row_combine
+  const bool wide = g.lc > 32;
+  const int gl = wide ? P.workers : g.lc;  // threads on the row
+  const int row = wide ? g.r0 : g.r0 + wk / g.lc;
+  const int lane = wide ? wk : (wk & (g.lc - 1));
   V a1 = V(0), a2 = V(0);
   if (row < g.r1) {
     int ja, jb;
@@ -255,12 +259,12 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += 4 * g.lc) {
+    for (int j0 = ja + lane; j0 < jb; j0 += 4 * gl) {
       int c[4];
       WT wv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int j = j0 + i * g.lc;
+        const int j = j0 + i * gl;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
         wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
@@ -278,10 +282,10 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
         }
     }
   }
-  *out1 = lane_group_sum(a1, g.lc);
-  if (NV > 1) *out2 = lane_group_sum(a2, g.lc);
+  *out1 = lane_group_sum(a1, wide ? 32 : g.lc);
+  if (NV > 1) *out2 = lane_group_sum(a2, wide ? 32 : g.lc);
   *row_out = row;
-  *lead = (row < g.r1) && lane == 0;
+  *lead = (row < g.r1) && (lane & (wide ? 31 : g.lc - 1)) == 0;
 }
 
 template <typename V, typename WT, bool SV, typename Val>
@@ -300,8 +304,10 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
                                              V* ap) {
   const RowUnit g = row_unit_geom<SV>(P, T, u, k);
   const bool ws = SV && g.wt != nullptr && static_cast<int>(sizeof(WT)) == T.wbytes;
-  const int row = g.r0 + wk / g.lc;
-  const int lane = wk & (g.lc - 1);
+  const bool wide = g.lc > 32;  // see row_gather_n
+  const int gl = wide ? P.workers : g.lc;
+  const int row = wide ? g.r0 : g.r0 + wk / g.lc;
+  const int lane = wide ? wk : (wk & (g.lc - 1));
   V a1 = V(0), a2 = V(0);
   if (row < g.r1) {
     int ja, jb;
@@ -312,12 +318,12 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += 4 * g.lc) {
+    for (int j0 = ja + lane; j0 < jb; j0 += 4 * gl) {
       int c[4];
       WT wv[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const int j = j0 + i * g.lc;
+        const int j = j0 + i * gl;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
         wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
@@ -337,10 +343,39 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
         }
     }
   }
-  *as = lane_group_sum(a1, g.lc);
-  *ap = lane_group_sum(a2, g.lc);
+  *as = lane_group_sum(a1, wide ? 32 : g.lc);
+  *ap = lane_group_sum(a2, wide ? 32 : g.lc);
   *row_out = row;
-  *lead = (row < g.r1) && lane == 0;
+  *lead = (row < g.r1) && (lane & (wide ? 31 : g.lc - 1)) == 0;
+}
+
+// Whether row unit u is wide (block-uniform: every thread reads the same
+// entry).
+__device__ __forceinline__ bool wide_unit(const DevPlan& P, int u) { return __ldg(P.ru_lanes + u) > 32; }
+
+// A wide unit's warps each hold a partial sum of its row (on the warp's lane
+// 0); thread wk = 0 adds them in warp order and becomes the row's only lead.
+// Called by every thread of the block (warp 0 included), so the two block
+// barriers are reached uniformly.
+template <int NGW, typename V>  // NGW = gather warps of the block
+__device__ __forceinline__ void wide_row_combine(int wk, V* a, V* b, bool* lead) {
+  __shared__ V wsum[2][NGW];
+  if (wk >= 0 && (wk & 31) == 0) {
+    wsum[0][wk >> 5] = *a;
+    wsum[1][wk >> 5] = *b;
+  }
+  __syncthreads();
+  if (wk == 0) {
+    V s1 = V(0), s2 = V(0);
+    for (int w = 0; w < NGW; ++w) {
+      s1 += wsum[0][w];
+      s2 += wsum[1][w];
+    }
+    *a = s1;
+    *b = s2;
+  }
+  *lead = wk == 0;
+  __syncthreads();
 }
 
 // Coefficient gather: acc = sum over grids l (this lane's share, l = lane,
@@ -506,6 +541,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       int k = 0, kg = 0, u0 = u;
       for (; u < nru; u += tm.G, ++k) {
         if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
+        if (wide_unit(P, u)) wide_row_combine<NW>(wk, &as, &ap, &lead);
         float part = 0.0f;
         if (wk >= 0 && lead) {
           const V qv = first ? as : fma(beta, ap, as);
@@ -964,11 +1000,13 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       if (!team_sync(tm)) return false;
       // r = b - A x  (FP64)
       for (int u = tm.rank, ku = 0; u < nru; u += tm.G, ++ku) {
-        if (wk < 0) continue;
         int row = 0;
         bool lead = false;
-        const double ax =
-            row_gather<double, double, SV>(P, T, P.wcsr, u, ku, wk, &row, &lead, [&](int m) { return ldcg(x + m); });
+        double ax = 0.0, unused = 0.0;
+        if (wk >= 0)
+          ax = row_gather<double, double, SV>(P, T, P.wcsr, u, ku, wk, &row, &lead,
+                                              [&](int m) { return ldcg(x + m); });
+        if (wide_unit(P, u)) wide_row_combine<BT / 32 - 1>(wk, &ax, &unused, &lead);
         if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
       }
       if (!team_sync(tm)) return false;

@@ -83,3 +83,38 @@ def test_sparse_support_D100_large_exact_recovery():
     plan.close()
     assert rep["status"] == 0, rep
     assert rel(c.cpu().numpy(), c_true) <= 1e-10
+
+
+@pytest.mark.parametrize("bt", [128, 256, 512])
+def test_wide_rows_match_oracle_and_batch(bt):
+    """Sparse supports put most columns in bin 0 of a grid: rows of more than
+    4 x 32 x 8 entries are gathered by every warp of a block (the warps'
+    partial sums added in a fixed order).  The plan must hold such rows, the
+    FP64 and mixed solves match the oracle, and a batch on small teams gives
+    the coefficients of the transform alone bit for bit."""
+    sup = W.sparse_infinity_support(12, 30, 9, 2000, 3)
+    N, D = sup.shape
+    sizes, nodes = W.l_grid(130, N, D, 3 * D, 1, 10)
+    params = W.gausscos_params(5, D)
+    f = O.sample_lgrid(W.FAMILY_GAUSSCOS, params, sup, sizes, nodes)
+    ref = O.fct(sup, sizes, nodes, f, "csne")
+    x = torch.from_numpy(f).cuda()
+    for opts, tol in ((dict(precision=F.FCT_FP64, tol=1e-14), 1e-11),
+                      (dict(precision=F.FCT_MIXED, tol=1e-13, inner_tol=1e-5), 1e-10)):
+        plan = F.Plan(sup, sizes, nodes, block_threads=bt, **opts)
+        lens = np.diff(F.fct_plan_tables(plan.handle)["rowptr"])
+        assert lens.max() > 4 * 32 * 8
+        c = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
+        rep = plan.execute(x, c)
+        assert rep["status"] == 0, rep
+        got = c.cpu().numpy()
+        assert rel(got, ref) <= tol, (rel(got, ref), rep)
+        clones = [plan.clone() for _ in range(3)]   # own workspace each
+        outs = [torch.full((N,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(3)]
+        reps = F.fct_execute_batch([p.handle for p in clones], [x] * 3, outs, team_blocks=4)
+        assert all(r["status"] == 0 for r in reps)
+        for o in outs:
+            assert torch.equal(o, c)
+        for p in clones:
+            p.close()
+        plan.close()
