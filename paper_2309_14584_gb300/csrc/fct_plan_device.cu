@@ -3,7 +3,8 @@
 // stacked over the L-grid as in Eq. (L-grid_A_mat), empty bins dropped).
 //
 // The same tables as the host builder, bit for bit:
-//   1. fold: one thread per (grid l, coefficient m) computes the global bin
+//   1. fold: one thread per (grid l, coefficient m) walks the nonzero
+//      components of m (listed once per coefficient) and computes the global bin
 //      key offsets[l] + bin_l(m) and the entry value (signed halves on the
 //      first-kind grid, T_m(xi) on single-point axes, multiplied in axis
 //      order with round-to-nearest and no contraction, as on the host);
@@ -64,22 +65,50 @@ __device__ __forceinline__ int lanes_for_dev(int32_t len, int epl) {
   return lanes;
 }
 
+// 0. nonzero components of every multi-index, in axis order: a zero
+// component folds to bin index 0 with entry 1 on every axis kind, so the fold
+// visits only the nonzero ones (sparse supports in high D have a few).
+// cnt[m] = their number (cnt[N] = 0, so the exclusive scan ends with the total).
+__global__ void nz_count_kernel(int64_t N, int D, const uint16_t* __restrict__ support, int32_t* __restrict__ cnt) {
+  for (int64_t m = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; m <= N;
+       m += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int32_t c = 0;
+    if (m < N)
+      for (int i = 0; i < D; ++i) c += support[m * D + i] != 0;
+    cnt[m] = c;
+  }
+}
+
+// pairs[nzoff[m] ..] = (axis << 16) | component, axis ascending.
+__global__ void nz_fill_kernel(int64_t N, int D, const uint16_t* __restrict__ support,
+                               const int32_t* __restrict__ nzoff, uint32_t* __restrict__ pairs) {
+  for (int64_t m = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; m < N;
+       m += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int32_t o = nzoff[m];
+    for (int i = 0; i < D; ++i) {
+      const uint32_t c = support[m * D + i];
+      if (c != 0) pairs[o++] = (static_cast<uint32_t>(i) << 16) | c;
+    }
+  }
+}
+
 // 1. fold.  e = l N + m (grid-major, so a warp shares one grid's sizes).
-__global__ void fold_kernel(int64_t KN, int64_t N, int D, const uint16_t* __restrict__ support,
-                            const int32_t* __restrict__ sizes, const int32_t* __restrict__ strides,
-                            const double* __restrict__ nodes, const int64_t* __restrict__ offsets, int first,
-                            int32_t* __restrict__ key, int32_t* __restrict__ val, double* __restrict__ weight) {
+__global__ void fold_kernel(int64_t KN, int64_t N, int D, const int32_t* __restrict__ nzoff,
+                            const uint32_t* __restrict__ pairs, const int32_t* __restrict__ sizes,
+                            const int32_t* __restrict__ strides, const double* __restrict__ nodes,
+                            const int64_t* __restrict__ offsets, int first, int32_t* __restrict__ key,
+                            int32_t* __restrict__ val, double* __restrict__ weight) {
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < KN;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t l = e / N, m = e - l * N;
-    const uint16_t* mi = support + m * D;
     const int32_t* sz = sizes + l * D;
     const int32_t* st = strides + l * D;
     int64_t bidx = 0;
     double w = 1.0;
-    for (int i = 0; i < D; ++i) {
-      const int64_t c = mi[i];
-      if (c == 0) continue;  // bin index 0, entry 1 on every axis kind
+    for (int32_t t = nzoff[m], te = nzoff[m + 1]; t < te; ++t) {
+      const uint32_t pr = pairs[t];
+      const int i = static_cast<int>(pr >> 16);
+      const int64_t c = pr & 0xffffu;
       const int64_t n = sz[i];
       if (n >= 2 && first) {
         // aliasing lemma: q = c div 2n, r = c mod 2n
@@ -446,10 +475,13 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   auto add = [&](void* dst, size_t bytes) { pieces.push_back({reinterpret_cast<void**>(dst), bytes}); };
   uint16_t* d_support;
   int32_t *d_sizes, *d_strides, *d_k0, *d_v0, *d_k1, *d_v1, *d_ghist, *d_part, *d_small;
-  int32_t *d_rowptr0, *d_rowsrc0, *d_rowgrid0, *d_col0, *d_crow0, *d_inv, *d_rowsrc;
+  int32_t *d_rowptr0, *d_rowsrc0, *d_rowgrid0, *d_col0, *d_crow0, *d_inv, *d_rowsrc, *d_nzoff;
+  uint32_t* d_pairs;
   double *d_nodes, *d_weight, *d_wcsr0;
   int64_t* d_offsets;
   add(&d_support, sizeof(uint16_t) * N * D);
+  add(&d_nzoff, sizeof(int32_t) * (N + 1));
+  add(&d_pairs, sizeof(uint32_t) * N * D);
   add(&d_sizes, sizeof(int32_t) * K * D);
   add(&d_strides, sizeof(int32_t) * K * D);
   add(&d_nodes, sizeof(double) * K * D);
@@ -507,10 +539,13 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
     return cuda_err(ue, "device table build upload");
   }
 
-  // 1. fold
-  fold_kernel<<<elem_blocks(KN), kElemThreads>>>(KN, N, D, d_support, d_sizes, d_strides, nodes ? d_nodes : nullptr,
-                                                 d_offsets, grid_kind == FCT_GRID_FIRST_KIND ? 1 : 0, d_k0, d_v0,
-                                                 d_weight);
+  // 0. nonzero components; 1. fold
+  nz_count_kernel<<<elem_blocks(N + 1), kElemThreads>>>(N, D, d_support, d_nzoff);
+  exclusive_scan(d_nzoff, d_nzoff, N + 1, d_part, d_small);
+  nz_fill_kernel<<<elem_blocks(N), kElemThreads>>>(N, D, d_support, d_nzoff, d_pairs);
+  fold_kernel<<<elem_blocks(KN), kElemThreads>>>(KN, N, D, d_nzoff, d_pairs, d_sizes, d_strides,
+                                                 nodes ? d_nodes : nullptr, d_offsets,
+                                                 grid_kind == FCT_GRID_FIRST_KIND ? 1 : 0, d_k0, d_v0, d_weight);
   // 2. stable sort by the global bin key (keys < M)
   int bits = 0;
   while (bits < 31 && ((H.M - 1) >> bits) > 0) ++bits;
