@@ -1021,6 +1021,13 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   row_units(H, workers, epl, &ru_first, &ru_lanes);
   final_pass_rows(H, &rowbase, &rowk);
   hp.n_row_units = static_cast<int32_t>(ru_lanes.size());
+  hp.n_wide_units = 0;
+  while (hp.n_wide_units < hp.n_row_units && ru_lanes[hp.n_wide_units] > 32) ++hp.n_wide_units;
+  for (int32_t u = hp.n_wide_units; u < hp.n_row_units; ++u)
+    if (ru_lanes[u] > 32) {
+      delete P;
+      return fail(FCT_ERR_INVALID_ARG, "internal: wide row units must come first");
+    }
   hp.n_mats = static_cast<int32_t>(H.dct_mats.size());
   hp.mats_smem = H.dct_mats.size() * sizeof(double) <= 32768 ? hp.n_mats : 0;
   P->ru_first = ru_first;

@@ -58,7 +58,7 @@ struct DevPlan {
   int32_t workers;           // gather threads per block (block threads - 32)
   int32_t mats_smem;         // doubles of DCT matrices to stage in shared memory (0 = read global)
   int32_t n_mats;            // doubles in dct_mats
-  int32_t pad0;
+  int32_t n_wide_units;      // leading row units that are wide rows (they sort first)
   // DCT
   const int32_t* pass_chunk_off;  // [npass + 1]
   const DctChunk* dct_chunks;

@@ -349,10 +349,8 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
   *lead = (row < g.r1) && (lane & (wide ? 31 : g.lc - 1)) == 0;
 }
 
-// Whether row unit u is wide (block-uniform: every thread reads the same
-// entry).
-__device__ __forceinline__ bool wide_unit(const DevPlan& P, int u) { return __ldg(P.ru_lanes + u) > 32; }
-
+// Wide rows sort first and are one unit each, so they are the first
+// P.n_wide_units row units: a block-uniform test with no memory access.
 // A wide unit's warps each hold a partial sum of its row (on the warp's lane
 // 0); thread wk = 0 adds them in warp order and becomes the row's only lead.
 // Called by every thread of the block (warp 0 included), so the two block
@@ -464,7 +462,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     if (!isfinite(gamma0)) *status_out = FCT_ERR_NONFINITE;
     return true;
   }
-  const int nru = P.n_row_units, ncc = P.n_coef_chunks;
+  const int nru = P.n_row_units, ncc = P.n_coef_chunks, nwide = P.n_wide_units;
   const int wk = static_cast<int>(threadIdx.x) - 32;  // worker index; warp 0 has wk < 0
   const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
   const int lane32 = threadIdx.x & 31;
@@ -541,7 +539,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       int k = 0, kg = 0, u0 = u;
       for (; u < nru; u += tm.G, ++k) {
         if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
-        if (wide_unit(P, u)) wide_row_combine<NW>(wk, &as, &ap, &lead);
+        if (u < nwide) wide_row_combine<NW>(wk, &as, &ap, &lead);
         float part = 0.0f;
         if (wk >= 0 && lead) {
           const V qv = first ? as : fma(beta, ap, as);
@@ -897,7 +895,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
   BlockTabs T;
   load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T, J.precision == FCT_MIXED && P.n_w_units > 0 && P.s_init == nullptr,
                       SV ? (J.precision == FCT_MIXED ? 4 : 8) : 0);
-  const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units;
+  const int ncc = P.n_coef_chunks, nre = P.n_rowel_chunks, nru = P.n_row_units, nwide = P.n_wide_units;
   const int wk = static_cast<int>(threadIdx.x) - 32;
   const int nce = (P.N + BT - 1) / BT;  // elementwise units over coefficients
   if (P.s_init != nullptr) {
@@ -1006,7 +1004,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         if (wk >= 0)
           ax = row_gather<double, double, SV>(P, T, P.wcsr, u, ku, wk, &row, &lead,
                                               [&](int m) { return ldcg(x + m); });
-        if (wide_unit(P, u)) wide_row_combine<BT / 32 - 1>(wk, &ax, &unused, &lead);
+        if (u < nwide) wide_row_combine<BT / 32 - 1>(wk, &ax, &unused, &lead);
         if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
       }
       if (!team_sync(tm)) return false;
