@@ -170,8 +170,12 @@ const char* fct_status_string(int status);
 
 /*
  * Build a plan: the alias tables of every grid (Sec. 3.3, Algorithm 2 without
- * its condition-number loop; the L-grid is an input), the DCT-I matrices and
- * the solver workspace, and upload them to the current device.
+ * its condition-number loop; the L-grid is an input; built by kernels on the
+ * current device unless opt->plan_build says host), the DCT-I matrices and the
+ * solver workspace, all resident on the current device.  The device build
+ * frees its scratch before returning, which waits for all work on the device
+ * (a running fct_server launch included): create plans before starting a
+ * server, as the serving engine does.
  *   D in [1, 255]; N >= 1; support host uint16[N][D] (any multi-indices);
  *   K >= 1; sizes host int32[K][D], every n in [1, 4096], each grid's point count and
  *   the total M below 2^31, K*N below 2^31; nodes host double[K][D] in [-1,1]
