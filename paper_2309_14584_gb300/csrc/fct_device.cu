@@ -1019,7 +1019,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
   std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
   row_units(H, workers, epl, &ru_first, &ru_lanes);
-  final_pass_rows(H, &rowbase, &rowk);
+  if (!on_device) final_pass_rows(H, &rowbase, &rowk);  // the device build made them
   hp.n_row_units = static_cast<int32_t>(ru_lanes.size());
   hp.n_wide_units = 0;
   while (hp.n_wide_units < hp.n_row_units && ru_lanes[hp.n_wide_units] > 32) ++hp.n_wide_units;
@@ -1202,9 +1202,9 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(d_chunks, H.dct_chunks.data(), sizeof(DctChunk) * H.dct_chunks.size()));
   chk(up(d_mats, H.dct_mats.data(), sizeof(double) * H.dct_mats.size()));
   chk(up(d_gfinal, H.gfinal.data(), sizeof(GridFinal) * K));
-  chk(up(d_rowbase, rowbase.data(), sizeof(int32_t) * H.R));
-  chk(up(d_rowk, rowk.data(), sizeof(int32_t) * H.R));
-  chk(up(d_rowgrid, H.rowgrid.data(), sizeof(int32_t) * H.R));
+  chk(up(d_rowbase, on_device ? static_cast<const void*>(DT.rowbase) : rowbase.data(), sizeof(int32_t) * H.R));
+  chk(up(d_rowk, on_device ? static_cast<const void*>(DT.rowk) : rowk.data(), sizeof(int32_t) * H.R));
+  chk(up(d_rowgrid, on_device ? static_cast<const void*>(DT.rowgrid) : H.rowgrid.data(), sizeof(int32_t) * H.R));
   chk(up(d_ru_first, ru_first.data(), sizeof(int32_t) * ru_first.size()));
   chk(up(d_ru_lanes, ru_lanes.data(), sizeof(int32_t) * ru_lanes.size()));
   chk(up(d_rowptr, H.rowptr.data(), sizeof(int32_t) * (H.R + 1)));

@@ -231,6 +231,8 @@ struct DeviceTables {
   void* mem = nullptr;
   int32_t* rowptr = nullptr;   // [R+1]
   int32_t* rowgrid = nullptr;  // [R]
+  int32_t* rowbase = nullptr;  // [R] last-pass fibre start of each row (as final_pass_rows)
+  int32_t* rowk = nullptr;     // [R] and the row's index along that fibre
   int32_t* col = nullptr;      // [K N] bin-major
   double* wcsr = nullptr;
   float* wcsr32 = nullptr;
@@ -242,9 +244,10 @@ struct DeviceTables {
 };
 
 // Builds the alias tables of H's plan on the current device (H holds the
-// offsets, D, K, N from build_host_tables(with_alias = false)).  Chooses the
-// entries per lane as the host path does (pick_entries_per_lane) and fills
-// H->R, H->rowptr, H->rowsrc and H->rowgrid in the device row order.
+// offsets, D, K, N and the DCT set-up from build_host_tables(with_alias =
+// false)).  Chooses the entries per lane as the host path does
+// (pick_entries_per_lane), fills H->R, H->rowptr and H->rowsrc in the device
+// row order, and out->rowbase / out->rowk as final_pass_rows would.
 fct_status build_device_tables(HostTables* H, const uint16_t* support, const int32_t* sizes, const double* nodes,
                                int grid_kind, int workers, int64_t wave, int fixed_epl, int* epl,
                                DeviceTables* out);

@@ -409,6 +409,22 @@ __global__ void coef_table_kernel(const int32_t* __restrict__ crow0, const int32
   }
 }
 
+// Per row, the start of its fibre in the grid's last DCT pass and its index
+// along that fibre (the same integer arithmetic as final_pass_rows).
+__global__ void final_rows_kernel(int64_t R, const int32_t* __restrict__ rowsrc, const int32_t* __restrict__ rowgrid,
+                                  const int64_t* __restrict__ offsets, const GridFinal* __restrict__ gfinal,
+                                  int32_t* __restrict__ rowbase, int32_t* __restrict__ rowk) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < R;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int l = rowgrid[r];
+    const GridFinal g = gfinal[l];
+    const int64_t bin = rowsrc[r] - offsets[l];
+    const int64_t k = (bin / g.stride) % g.n;
+    rowbase[r] = static_cast<int32_t>(offsets[l] + bin - k * g.stride);
+    rowk[r] = static_cast<int32_t>(k);
+  }
+}
+
 __global__ void set_int_kernel(int32_t* dst, int32_t v) { *dst = v; }
 
 fct_status cuda_err(cudaError_t e, const char* what) {
@@ -479,6 +495,7 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   uint32_t* d_pairs;
   double *d_nodes, *d_weight, *d_wcsr0;
   int64_t* d_offsets;
+  GridFinal* d_gfinal;
   add(&d_support, sizeof(uint16_t) * N * D);
   add(&d_nzoff, sizeof(int32_t) * (N + 1));
   add(&d_pairs, sizeof(uint32_t) * N * D);
@@ -486,6 +503,7 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   add(&d_strides, sizeof(int32_t) * K * D);
   add(&d_nodes, sizeof(double) * K * D);
   add(&d_offsets, sizeof(int64_t) * (K + 1));
+  add(&d_gfinal, sizeof(GridFinal) * K);
   add(&d_k0, sizeof(int32_t) * KN);
   add(&d_v0, sizeof(int32_t) * KN);
   add(&d_k1, sizeof(int32_t) * KN);
@@ -504,6 +522,8 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   add(&d_rowsrc, sizeof(int32_t) * KN);
   add(&out->rowptr, sizeof(int32_t) * (KN + 1));
   add(&out->rowgrid, sizeof(int32_t) * KN);
+  add(&out->rowbase, sizeof(int32_t) * KN);
+  add(&out->rowk, sizeof(int32_t) * KN);
   add(&out->col, sizeof(int32_t) * KN);
   add(&out->wcsr, sizeof(double) * KN);
   add(&out->wcsr32, sizeof(float) * KN);
@@ -534,6 +554,11 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   chk(cudaMemcpy(d_strides, strides.data(), sizeof(int32_t) * K * D, cudaMemcpyHostToDevice));
   if (nodes) chk(cudaMemcpy(d_nodes, nodes, sizeof(double) * K * D, cudaMemcpyHostToDevice));
   chk(cudaMemcpy(d_offsets, H.offsets.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice));
+  if (static_cast<int>(H.gfinal.size()) != K) {
+    out->release();
+    return fail(FCT_ERR_INVALID_ARG, "internal: device table build needs the DCT set-up");
+  }
+  chk(cudaMemcpy(d_gfinal, H.gfinal.data(), sizeof(GridFinal) * K, cudaMemcpyHostToDevice));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build upload");
@@ -598,15 +623,16 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   entry_perm_kernel<<<elem_blocks(KN), kElemThreads>>>(out->rowptr, R, order, d_rowptr0, d_col0, d_wcsr0, KN,
                                                        out->col, out->wcsr, out->wcsr32);
   coef_table_kernel<<<elem_blocks(KN), kElemThreads>>>(d_crow0, d_inv, d_weight, KN, out->crow, out->wcm32);
+  final_rows_kernel<<<elem_blocks(R), kElemThreads>>>(R, d_rowsrc, out->rowgrid, d_offsets, d_gfinal, out->rowbase,
+                                                      out->rowk);
   chk(cudaGetLastError());
 
   H.R = R;
   H.rowptr.assign(R + 1, 0);
   H.rowsrc.assign(R, 0);
-  H.rowgrid.assign(R, 0);
+  H.rowgrid.clear();  // stays on the device (out->rowgrid)
   chk(cudaMemcpy(H.rowptr.data(), out->rowptr, sizeof(int32_t) * (R + 1), cudaMemcpyDeviceToHost));
   chk(cudaMemcpy(H.rowsrc.data(), d_rowsrc, sizeof(int32_t) * R, cudaMemcpyDeviceToHost));
-  chk(cudaMemcpy(H.rowgrid.data(), out->rowgrid, sizeof(int32_t) * R, cudaMemcpyDeviceToHost));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build (row order)");
