@@ -555,7 +555,14 @@ def construct_alias_system(support, cand_sizes, cand_nodes, kappa0: float = 1e4)
 
 
 def numerical_rank(A, rtol: float = 1e-10) -> int:
-    AtA = (A.T @ A)
-    AtA = AtA.toarray() if sp.issparse(AtA) else AtA
-    ev = np.linalg.eigvalsh(AtA)
-    return int((ev > ev[-1] * rtol * rtol).sum())
+    """Number of singular values of A above rtol * sigma_max (the definition
+    of numerical rank; the singular values come from the dense SVD of A
+    itself, since the eigenvalues of A^T A cannot resolve sigma below about
+    1e-8 sigma_max)."""
+    A = A.toarray() if sp.issparse(A) else np.asarray(A, dtype=np.float64)
+    if A.size == 0:
+        return 0
+    sv = np.linalg.svd(A, compute_uv=False)
+    if sv[0] == 0.0:
+        return 0
+    return int((sv > sv[0] * rtol).sum())

@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 
+import workloads as W
 from oracle import fct_oracle as O
 from tests import test_oracle_pins as P
 
@@ -128,7 +129,54 @@ def _eval_axes_swapped(coeffs, support, points):
     return _orig_eval(coeffs, support, np.atleast_2d(points)[:, ::-1])
 
 
+_orig_sample_grid = O.sample_grid
+
+
+def _sampler_variant(cos_arg_squared=False, drop_a=False, drop_c=False, rational_unsquared=False):
+    def sample_grid(family, params, support, axes):
+        D = len(axes)
+        shape = tuple(a.size for a in axes)
+        bc = O._broadcast_axis
+        if family in (W.FAMILY_GAUSSCOS, W.FAMILY_POLY_GAUSSCOS):
+            a, b = params[:D], params[D:2 * D]
+            quad = sum((1.0 if drop_a else a[i]) * bc(axes[i] ** 2, i, D) for i in range(D))
+            lin = sum(b[i] * bc(axes[i] ** 2 if cos_arg_squared else axes[i], i, D) for i in range(D))
+            return np.broadcast_to(np.exp(-quad) * np.cos(lin), shape).copy()
+        if family == W.FAMILY_RATIONAL:
+            c = params[:D]
+            quad = sum((1.0 if drop_c else c[i]) * bc(axes[i] if rational_unsquared else axes[i] ** 2, i, D)
+                       for i in range(D))
+            return np.broadcast_to(1.0 / (1.0 + quad), shape).copy()
+        return _orig_sample_grid(family, params, support, axes)
+    return sample_grid
+
+
+def _rank_from_normal_eigenvalues(A, rtol=1e-10):
+    A = A.toarray() if hasattr(A, "toarray") else np.asarray(A)
+    ev = np.linalg.eigvalsh(A.T @ A)
+    return int((ev > ev[-1] * rtol * rtol).sum())
+
+
+def _rank_rtol_unsquared(A, rtol=1e-10):
+    A = A.toarray() if hasattr(A, "toarray") else np.asarray(A)
+    sv = np.linalg.svd(A, compute_uv=False)
+    return int((sv * sv > sv[0] * sv[0] * rtol).sum()) if sv.size and sv[0] > 0 else 0
+
+
+def _golden_sampler_pins():
+    for fam in ("gausscos", "rational", "runge"):
+        P.test_sampler_families_match_hand_values(fam)
+
+
 MUTATIONS = [
+    ("gausscos_cos_of_squares", "sample_grid", _sampler_variant(cos_arg_squared=True), _golden_sampler_pins),
+    ("gausscos_a_dropped", "sample_grid", _sampler_variant(drop_a=True), _golden_sampler_pins),
+    ("rational_c_dropped", "sample_grid", _sampler_variant(drop_c=True), _golden_sampler_pins),
+    ("rational_unsquared", "sample_grid", _sampler_variant(rational_unsquared=True), _golden_sampler_pins),
+    ("rank_from_normal_eigenvalues", "numerical_rank", _rank_from_normal_eigenvalues,
+     lambda: P.test_numerical_rank_of_constructed_matrices()),
+    ("rank_rtol_unsquared", "numerical_rank", _rank_rtol_unsquared,
+     lambda: P.test_numerical_rank_of_constructed_matrices()),
     ("fold_off_by_one", "fold", _fold_off_by_one, lambda: P.test_fold_identity_exhaustive()),
     ("fold_off_by_one_recovery", "fold", _fold_off_by_one,
      lambda: P.test_exact_recovery_of_polynomials_in_support(*P.RECOVERY[1])),

@@ -266,6 +266,103 @@ def test_solver_tiers_agree_and_are_optimal():
     assert np.linalg.norm(g) <= 1e-13 * np.linalg.norm(s.A.T @ b)
 
 
+# ---------------------------------------------------------------- samplers
+def _golden_samples():
+    rows = {}
+    for line in open(os.path.join(GOLDEN, "sampler_values.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        fam, idx, val, _ = [t.strip() for t in line.split("|")]
+        i0, i1 = (int(t) for t in idx.split())
+        rows.setdefault(fam, {})[(i0, i1)] = float(val)
+    return rows
+
+
+# the hand-picked grid of the golden file: n = 4, n = 3, one point at xi = 1/2
+_GOLDEN_SIZES = np.array([4, 3, 1], dtype=np.int32)
+_GOLDEN_NODES = np.array([0.0, 0.0, 0.5])
+_GOLDEN_PARAMS = {
+    "gausscos": (W.FAMILY_GAUSSCOS, np.array([0.5, 0.25, 1.0, 1.0, 2.0, 0.5])),
+    "rational": (W.FAMILY_RATIONAL, np.array([0.5, 0.25, 1.0])),
+    "runge": (W.FAMILY_RATIONAL, np.array([10.0, 10.0, 10.0])),
+}
+
+
+@pytest.mark.parametrize("family", ["gausscos", "rational", "runge"])
+def test_sampler_families_match_hand_values(family):
+    """The analytic targets on a small grid equal values worked out by hand
+    (tests/golden/sampler_values.txt); the Runge case is the paper's f_1
+    (Sec. 4, Function Class #1) on that grid."""
+    fam, params = _GOLDEN_PARAMS[family]
+    want = _golden_samples()[family]
+    sup = np.zeros((1, 3), dtype=np.uint16)
+    got = O.sample_grid(fam, params, sup, O.grid_axes(_GOLDEN_SIZES, _GOLDEN_NODES))
+    assert got.shape == (4, 3, 1)
+    assert len(want) == 12
+    for (i0, i1), v in want.items():
+        assert abs(got[i0, i1, 0] - v) <= 2e-16 * max(1.0, abs(v)), (family, i0, i1, got[i0, i1, 0], v)
+
+
+@pytest.mark.parametrize("D", [1, 4, 9])
+def test_sampler_families_at_the_origin_and_on_an_axis(D):
+    """Special cases: both families are 1 at x = 0; with x = t e_k the
+    Gaussian-cosine reduces to exp(-a_k t^2) cos(b_k t) and the rational form
+    to 1 / (1 + c_k t^2), independent of the other parameters."""
+    g = W.stream(31, "probe")
+    sizes = np.ones(D, dtype=np.int32)
+    gp = W.gausscos_params(7, D)
+    rp = W.rational_params(7, D)
+    sup = np.zeros((1, D), dtype=np.uint16)
+    zero = O.grid_axes(sizes, np.zeros(D))
+    assert O.sample_grid(W.FAMILY_GAUSSCOS, gp, sup, zero).item() == 1.0
+    assert O.sample_grid(W.FAMILY_RATIONAL, rp, sup, zero).item() == 1.0
+    for k in range(D):
+        t = float(g.uniform(-1.0, 1.0))
+        nodes = np.zeros(D)
+        nodes[k] = t
+        axes = O.grid_axes(sizes, nodes)
+        want_g = math.exp(-gp[k] * t * t) * math.cos(gp[D + k] * t)
+        want_r = 1.0 / (1.0 + rp[k] * t * t)
+        assert abs(O.sample_grid(W.FAMILY_GAUSSCOS, gp, sup, axes).item() - want_g) <= 1e-15
+        assert abs(O.sample_grid(W.FAMILY_RATIONAL, rp, sup, axes).item() - want_r) <= 1e-15
+
+
+def test_sampler_poly_gausscos_is_the_sum_of_its_parts():
+    """The combined family is the Gaussian-cosine plus the polynomial."""
+    D, d = 3, 4
+    sup = W.total_degree_support(D, d)
+    axes = O.grid_axes(np.array([5, 1, 4]), np.array([0.0, 0.3, 0.0]))
+    gp = W.gausscos_params(3, D)
+    c = W.poly_coefficients(3, sup)
+    both = O.sample_grid(W.FAMILY_POLY_GAUSSCOS, np.concatenate([gp, c]), sup, axes)
+    parts = O.sample_grid(W.FAMILY_GAUSSCOS, gp, sup, axes) + O.sample_grid(W.FAMILY_POLY, c, sup, axes)
+    assert np.array_equal(both, parts)
+
+
+def _matrix_with_singular_values(sv, rows, seed):
+    """U diag(sv) V^T with random orthogonal U (rows x n) and V (n x n)."""
+    g = W.stream(seed, "probe")
+    n = len(sv)
+    U, _ = np.linalg.qr(g.standard_normal((rows, n)))
+    V, _ = np.linalg.qr(g.standard_normal((n, n)))
+    return (U * np.asarray(sv)) @ V.T
+
+
+def test_numerical_rank_of_constructed_matrices():
+    """rank = number of singular values above rtol * sigma_max: exact on
+    matrices built with known singular values (including ones too small for
+    the eigenvalues of A^T A to resolve)."""
+    sv = [1.0, 1e-3, 1e-6, 1e-9, 1e-12, 0.0, 0.0]
+    A = _matrix_with_singular_values(sv, 12, 5)
+    assert O.numerical_rank(A, rtol=1e-10) == 4
+    assert O.numerical_rank(A, rtol=1e-7) == 3
+    assert O.numerical_rank(A, rtol=1e-4) == 2
+    assert O.numerical_rank(A, rtol=1e-2) == 1
+    assert O.numerical_rank(_matrix_with_singular_values([2.0] * 6, 9, 6)) == 6
+    assert O.numerical_rank(np.zeros((5, 3))) == 0
+
+
 def test_rank_deficient_plan_is_detected():
     """All grids sharing one single-point node at x = 1 on the same axis: the
     polynomial T_1(x_0) - 1 vanishes on every grid, so A loses rank and the
@@ -276,7 +373,9 @@ def test_rank_deficient_plan_is_detected():
     s = O.AliasSystem(sup, sizes, np.ones((3, D)))
     with pytest.raises(O.RankDeficient):
         O.householder_lstsq(s.A.toarray(), np.ones(s.R))
-    assert O.numerical_rank(s.A) < sup.shape[0]
+    # T_{m_0}(1) = 1, so every column depends on m_1 alone; the four values
+    # m_1 = 0..3 fold to distinct bins of the 5-point axis: rank exactly 4
+    assert O.numerical_rank(s.A) == 4
 
 
 # ---------------------------------------------------------------- workloads
