@@ -110,18 +110,6 @@ typedef struct {
                          it.  Larger values mean fewer, longer units: better when
                          the plan runs on small teams (fct_execute_batch, serving),
                          where a block works through many units one after another. */
-  int cluster_solve;  /* FCT_MIXED: 1 = after the DCT and b (whole GPU), run the solve in one
-                         thread-block cluster (16 blocks, one per SM) whose blocks hold
-                         the FP32 tables and the vectors in shared memory, gather
-                         through distributed shared memory and synchronise with
-                         cluster barriers; used by fct_execute / fct_execute_host
-                         when every block's slice fits (fct_plan_info.cluster_blocks
-                         says whether it does), else the team solver.  0 (default) =
-                         team solver.  Batches, serving and fct_execute_noalloc use
-                         the team solver.  With normal_matrix = 0 (auto), asking for
-                         the cluster solver keeps the plan from storing W.  Measured
-                         on GB300 it only matches the team solver on very small plans
-                         (N ~ 150) and is 3-4x slower at N >= 1e3.                   */
   int plan_build;     /* where fct_plan_create builds the alias tables: FCT_PLAN_BUILD_AUTO
                          (0, default) and FCT_PLAN_BUILD_DEVICE (2) on the GPU (fold,
                          stable radix sort by bin, compaction, row order: kernels),
@@ -155,7 +143,6 @@ typedef struct {
   int32_t coef_lanes;
   int64_t device_bytes;     /* tables + workspace held on the device               */
   int64_t normal_nnz;       /* nonzeros of W = A^T A when the plan stores it, else 0 */
-  int64_t cluster_blocks;   /* blocks of the cluster solver fct_execute uses, else 0 */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,
@@ -260,11 +247,16 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
  *   - Plans whose workspace exceeds 32 MiB are rejected with
  *     FCT_ERR_INVALID_ARG (the message gives the bytes needed).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *     that first call before any stream capture.  A process that resets the
+ *     device (cudaDeviceReset) must not call this entry point afterwards.
  *   - All calls on a device share the array: calls that overlap on the GPU
  *     (different streams, or different plans at once) race and must not be
  *     issued.  The array keeps the last call's contents; the call clears what
  *     must start at zero itself.
+ *   - The solve always runs on the team solver with its index tables staged in
+ *     shared memory (fct_execute may also stage the entry values): results
+ *     equal fct_execute's up to rounding.
  */
 fct_status fct_execute_noalloc(fct_plan plan, const double* samples, double* coeffs, void* stream,
                                fct_report* rep);

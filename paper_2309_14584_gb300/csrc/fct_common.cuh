@@ -117,10 +117,10 @@ static __device__ void team_exit(const Team& tm) {
 // the last nk units (wpart); warp 0 stores the unit partials part[u0 + i*G]
 // and its lane 0 arrives at and waits on the team barrier, so one block-wide
 // sync before and one after cover both the flush and the barrier.
-__device__ __forceinline__ float padd(float a, float b) { return a + b; }
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float pzero(float) { return 0.0f; }
-__device__ __forceinline__ float2 pzero(float2) { return make_float2(0.0f, 0.0f); }
+__device__ __forceinline__ double padd(double a, double b) { return a + b; }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double pzero(double) { return 0.0; }
+__device__ __forceinline__ double2 pzero(double2) { return make_double2(0.0, 0.0); }
 
 template <int NW, typename PT>
 __device__ bool phase_end(Team& tm, const PT (*wpart)[NW], PT* part, int u0, int nk) {
@@ -186,29 +186,30 @@ __device__ __forceinline__ void warp0_team_sum(const double* part, int n, double
   if (threadIdx.x == 0) red[BT / 32] = v;
 }
 
-// Warp 0: FP32 sum of n chunk partials in a fixed order, left in *out (lane 0).
-__device__ __forceinline__ float warp0_team_sum_f(const float* part, int n) {
-  // 16 independent loads per lane per round: up to 512 partials in one L2 round trip
-  float v = 0.0f;
-  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 16) {
-    float t[16];
+// Warp 0: FP64 sum of n per-unit partials in a fixed order (lane 0 holds
+// the result): 8 independent loads per lane per round, so up to 256
+// partials come back in one L2 round trip.
+__device__ __forceinline__ double warp0_sum(const double* part, int n) {
+  double v = 0.0;
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
+    double t[8];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0f;
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0;
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v += t[j];
+    for (int j = 0; j < 8; ++j) v += t[j];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// Warp 0: FP32 pair sums of n partials in a fixed order (lane 0 holds the result).
-__device__ __forceinline__ float2 warp0_team_sum_f2(const float2* part, int n) {
-  float2 v = make_float2(0.0f, 0.0f);
+// Warp 0: FP64 pair sums of n partials in a fixed order (lane 0 holds the result).
+__device__ __forceinline__ double2 warp0_sum(const double2* part, int n) {
+  double2 v = make_double2(0.0, 0.0);
   for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 4) {
-    float2 t[4];
+    double2 t[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_float2(0.0f, 0.0f);
+    for (int j = 0; j < 4; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_double2(0.0, 0.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) v = padd(v, t[j]);
   }

@@ -16,7 +16,6 @@
 // elementwise updates.  All reductions are two-stage with a fixed order
 // (per-chunk block sums, then one sum over chunk partials), so a transform's
 // result does not depend on the team size or on the rest of the batch.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,384 +30,6 @@
 #include <vector>
 
 #include "fct_common.cuh"
-
-// ---------------------------------------------------------------------------
-// Cluster solver of the mixed path.  After the team kernel has formed b and
-// g = A^T b, one thread-block cluster (cl_cs blocks, one per SM) runs the
-// rest of the mixed solve: FP32 inner CG on the normal equations, FP64 sweeps
-// g = A^T (b - A x), and the FP64 continuation.  Each block holds its slice of
-// the tables (rows split by entry count, coefficients in chunks of cl_nc) and
-// of the vectors in shared memory; gathers read other blocks' vectors through
-// distributed shared memory, and the two synchronisations of a CG iteration
-// are hardware cluster barriers instead of global-memory team barriers.
-// Every block takes every decision from the same cluster-wide sums (a fixed
-// order), so all blocks pass the same barriers.
-// ---------------------------------------------------------------------------
-namespace cgx = cooperative_groups;
-
-constexpr int kClusterThreads = 512;
-constexpr int kMaxCluster = 16;
-
-struct ClusterArgs {
-  const DevPlan* plan;
-  double* coeffs;
-  fct_report* report;
-  double tol, inner_tol;
-  int max_iter, max_refine;
-};
-
-// Byte offsets in a block's shared memory.  The first part (exchange slots,
-// {s, p} in FP32 and FP64, x, the row vector q / r) sits at the same offsets
-// in every block, since other blocks read it; the table slices follow.
-struct ClusterLayout {
-  int slots, sp32, x64, qr, sp64;
-  int rowptr, col, crow, w32r, w32c, dx32, g64, end;
-};
-
-__host__ __device__ inline int align16i(int64_t x) { return static_cast<int>((x + 15) & ~int64_t{15}); }
-
-__host__ __device__ inline ClusterLayout cluster_layout(int nc, int maxrows, int nr, int ne, int nm, int K,
-                                                       int wsmem) {
-  ClusterLayout L;
-  int o = 0;
-  L.slots = o;
-  o += align16i(kMaxCluster * (4 + 4 + 8 + 8));  // float A, float B, double D0, double D1
-  L.sp32 = o;
-  o += align16i(int64_t{nc} * 8);
-  L.x64 = o;
-  o += align16i(int64_t{nc} * 8);
-  L.qr = o;
-  o += align16i(int64_t{maxrows} * 8);
-  L.sp64 = o;
-  o += align16i(int64_t{nc} * 16);
-  L.rowptr = o;
-  o += align16i(int64_t{nr + 1} * 4);
-  L.col = o;
-  o += align16i(int64_t{ne} * 4);
-  L.crow = o;
-  o += align16i(int64_t{nm} * K * 4);
-  L.w32r = o;
-  o += wsmem ? align16i(int64_t{ne} * 4) : 0;
-  L.w32c = o;
-  o += wsmem ? align16i(int64_t{nm} * K * 4) : 0;
-  L.dx32 = o;
-  o += align16i(int64_t{nc} * 4);
-  L.g64 = o;
-  o += align16i(int64_t{nc} * 8);
-  L.end = o;
-  return L;
-}
-
-struct ClusterCtx {
-  const DevPlan* P;
-  unsigned char* const* rb;  // generic address of every block's shared memory
-  unsigned char* sm;         // this block's
-  ClusterLayout L;
-  int rank, CS, nr, ne, nm, m0, e0, r0;
-  double* red;
-  int* nd;                   // double-slot alternation counter (block-uniform)
-};
-
-// owner block (high 8 bits) and local index (low 24 bits) of a packed index
-__device__ __forceinline__ int cl_owner(int pk) { return static_cast<unsigned int>(pk) >> 24; }
-__device__ __forceinline__ int cl_local(int pk) { return pk & 0xffffff; }
-
-template <typename T>
-__device__ __forceinline__ T cl_remote(const ClusterCtx& c, int off, int pk) {
-  return *reinterpret_cast<const T*>(c.rb[cl_owner(pk)] + off + static_cast<size_t>(cl_local(pk)) * sizeof(T));
-}
-
-// Block sum of v (fixed order), valid in every thread.
-__device__ double cl_block_sum(const ClusterCtx& c, double v) {
-  v = warp_sum(v);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) c.red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  for (int w = 0; w < kClusterThreads / 32; ++w) t += c.red[w];
-  return t;
-}
-
-// Cluster sum: every block's total goes to slot [rank] of every block, then
-// one cluster barrier; all threads add the slots in rank order.
-__device__ double cl_sum_d(const ClusterCtx& c, double v) {
-  const double t = cl_block_sum(c, v);
-  const int buf = (*c.nd)++ & 1;
-  const int off = c.L.slots + kMaxCluster * 8 + buf * kMaxCluster * 8;
-  if (threadIdx.x < c.CS) reinterpret_cast<double*>(c.rb[threadIdx.x] + off)[c.rank] = t;
-  cgx::this_cluster().sync();
-  const double* sl = reinterpret_cast<const double*>(c.sm + off);
-  double s = 0.0;
-  for (int j = 0; j < c.CS; ++j) s += sl[j];
-  return s;
-}
-
-__device__ float cl_sum_f(const ClusterCtx& c, float v, int which) {
-  const float t = static_cast<float>(cl_block_sum(c, static_cast<double>(v)));
-  const int off = c.L.slots + which * kMaxCluster * 4;
-  if (threadIdx.x < c.CS) reinterpret_cast<float*>(c.rb[threadIdx.x] + off)[c.rank] = t;
-  cgx::this_cluster().sync();
-  const float* sl = reinterpret_cast<const float*>(c.sm + off);
-  float s = 0.0f;
-  for (int j = 0; j < c.CS; ++j) s += sl[j];
-  return s;
-}
-
-// CG on the normal equations A^T A x = s0 (s0 in sp.x, p = 0 on entry), the
-// same recurrences and stopping rules as cg_normal.  V = float: FP32 tables
-// (shared memory when WS, else global); V = double: FP64 tables from global
-// memory.  q lives at L.qr (rows), {s, p} at the V2 offset, x is local.
-template <typename V, bool WS>
-__device__ int cluster_cgne(const ClusterCtx& c, V* x, double gamma0, double tol, int max_iter, int stall,
-                            int* iters_out, double* gamma_out) {
-  using V2 = typename Vec2<V>::T;
-  const DevPlan& P = *c.P;
-  const int T = kClusterThreads, tid = threadIdx.x;
-  const int off_sp = sizeof(V) == 4 ? c.L.sp32 : c.L.sp64;
-  V2* sp = reinterpret_cast<V2*>(c.sm + off_sp);
-  V* q = reinterpret_cast<V*>(c.sm + c.L.qr);
-  const int* rowptr = reinterpret_cast<const int*>(c.sm + c.L.rowptr);
-  const int* col = reinterpret_cast<const int*>(c.sm + c.L.col);
-  const int* crow = reinterpret_cast<const int*>(c.sm + c.L.crow);
-  const float* w32r = reinterpret_cast<const float*>(c.sm + c.L.w32r);
-  const float* w32c = reinterpret_cast<const float*>(c.sm + c.L.w32c);
-  const int nm = c.nm, N = P.N, K = P.K;
-  auto wrow = [&](int j) -> V {
-    if constexpr (sizeof(V) == 4) return WS ? w32r[j] : __ldg(P.wcsr32 + c.e0 + j);
-    else return __ldg(P.wcsr + c.e0 + j);
-  };
-  auto wcoef = [&](int l, int i) -> V {
-    if constexpr (sizeof(V) == 4) return WS ? w32c[l * nm + i] : __ldg(P.wcm32 + static_cast<int64_t>(l) * N + c.m0 + i);
-    else return __ldg(P.wcm + static_cast<int64_t>(l) * N + c.m0 + i);
-  };
-  *iters_out = 0;
-  *gamma_out = gamma0;
-  if (!(gamma0 > 0.0) || !isfinite(gamma0)) return isfinite(gamma0) ? FCT_OK : FCT_ERR_NONFINITE;
-  const V rs = static_cast<V>(1.0 / sqrt(gamma0));
-  const float tol2 = static_cast<float>(tol * tol);
-  auto relsq = [&](V v) {
-    const float t = static_cast<float>(v * rs);
-    return t * t;
-  };
-  float gam = 1.0f, best = 1.0f, beta = 0.0f;
-  int it = 0, best_it = 0, status = FCT_OK;
-  bool first = true;
-  for (;;) {
-    // phase A: q = A s + beta A p over this block's rows
-    float part = 0.0f;
-    for (int r = tid; r < c.nr; r += T) {
-      V as = V(0), ap = V(0);
-      const int j1 = rowptr[r + 1];
-#pragma unroll 4
-      for (int j = rowptr[r]; j < j1; ++j) {
-        const V w = wrow(j);
-        const V2 v = cl_remote<V2>(c, off_sp, col[j]);
-        as = fma(w, v.x, as);
-        ap = fma(w, v.y, ap);
-      }
-      const V qv = first ? as : fma(static_cast<V>(beta), ap, as);
-      q[r] = qv;
-      part += relsq(qv);
-    }
-    const float dl = cl_sum_f(c, part, 0);
-    if (!isfinite(dl)) {
-      status = FCT_ERR_NONFINITE;
-      break;
-    }
-    if (!(dl > 0.0f)) break;  // q = 0: s is already zero to working precision
-    const float al = gam / dl;
-    // phase B: t = A^T q; owner updates {s, p} and x
-    part = 0.0f;
-    for (int i = tid; i < nm; i += T) {
-      V t = V(0);
-#pragma unroll 6
-      for (int l = 0; l < K; ++l) t = fma(wcoef(l, i), cl_remote<V>(c, c.L.qr, crow[l * nm + i]), t);
-      const V2 o = sp[i];
-      const V pn = first ? o.x : fma(static_cast<V>(beta), o.y, o.x);
-      const V sn = fma(-static_cast<V>(al), t, o.x);
-      V2 nv;
-      nv.x = sn;
-      nv.y = pn;
-      sp[i] = nv;
-      x[i] = fma(static_cast<V>(al), pn, x[i]);
-      part += relsq(sn);
-    }
-    const float gnew = cl_sum_f(c, part, 1);
-    ++it;
-    first = false;
-    if (!isfinite(gnew)) {
-      status = FCT_ERR_NONFINITE;
-      break;
-    }
-    beta = gnew / gam;
-    gam = gnew;
-    if (gam <= tol2) break;
-    if (it >= max_iter) {
-      status = FCT_ERR_NOCONV;
-      break;
-    }
-    if (stall > 0) {
-      if (gam < best) {
-        best = gam;
-        best_it = it;
-      } else if (it - best_it >= stall) {
-        break;
-      }
-    }
-  }
-  *iters_out = it;
-  *gamma_out = static_cast<double>(gam) * gamma0;
-  return status;
-}
-
-__global__ void __launch_bounds__(kClusterThreads, 1) cluster_solve_kernel(const ClusterArgs a) {
-  cgx::cluster_group cl = cgx::this_cluster();
-  extern __shared__ __align__(16) unsigned char csm[];
-  __shared__ unsigned char* rb[kMaxCluster];
-  __shared__ double red[kClusterThreads / 32];
-  __shared__ int rows_s[kMaxCluster + 1];
-  const DevPlan& P = *a.plan;
-  const int CS = P.cl_cs, rank = static_cast<int>(cl.block_rank());
-  const int N = P.N, K = P.K, nc = P.cl_nc, tid = threadIdx.x, T = kClusterThreads;
-  if (tid <= CS) rows_s[tid] = P.cl_rows[tid];
-  if (tid < CS) rb[tid] = static_cast<unsigned char*>(cl.map_shared_rank(static_cast<void*>(csm), tid));
-  __syncthreads();
-  const int r0 = rows_s[rank], r1 = rows_s[rank + 1];
-  const int e0 = P.rowptr[r0], e1 = P.rowptr[r1];
-  const int m0 = rank * nc, m1 = min(N, m0 + nc);
-  int nd = 0;
-  ClusterCtx c;
-  c.P = &P;
-  c.rb = rb;
-  c.sm = csm;
-  c.rank = rank;
-  c.CS = CS;
-  c.nr = r1 - r0;
-  c.ne = e1 - e0;
-  c.nm = max(0, m1 - m0);
-  c.m0 = m0;
-  c.e0 = e0;
-  c.r0 = r0;
-  c.red = red;
-  c.nd = &nd;
-  c.L = cluster_layout(nc, P.cl_maxrows, c.nr, c.ne, c.nm, K, P.cl_w_smem);
-  const ClusterLayout& L = c.L;
-  int* rowptr = reinterpret_cast<int*>(csm + L.rowptr);
-  int* col = reinterpret_cast<int*>(csm + L.col);
-  int* crow = reinterpret_cast<int*>(csm + L.crow);
-  float* w32r = reinterpret_cast<float*>(csm + L.w32r);
-  float* w32c = reinterpret_cast<float*>(csm + L.w32c);
-  float2* sp32 = reinterpret_cast<float2*>(csm + L.sp32);
-  double2* sp64 = reinterpret_cast<double2*>(csm + L.sp64);
-  double* x64 = reinterpret_cast<double*>(csm + L.x64);
-  double* qr = reinterpret_cast<double*>(csm + L.qr);
-  float* dx32 = reinterpret_cast<float*>(csm + L.dx32);
-  double* g64 = reinterpret_cast<double*>(csm + L.g64);
-  const int nm = c.nm, nr = c.nr, ne = c.ne;
-  // ---- stage this block's slices; pack (owner, local) indices
-  for (int i = tid; i <= nr; i += T) rowptr[i] = P.rowptr[r0 + i] - e0;
-  for (int j = tid; j < ne; j += T) {
-    const int cc = P.col[e0 + j], own = cc / nc;
-    col[j] = (own << 24) | (cc - own * nc);
-    if (P.cl_w_smem) w32r[j] = P.wcsr32[e0 + j];
-  }
-  for (int idx = tid; idx < nm * K; idx += T) {
-    const int l = idx / nm, i = idx - l * nm;
-    const int row = P.crow[static_cast<int64_t>(l) * N + m0 + i];
-    int own = 0;
-    while (own + 1 < CS && rows_s[own + 1] <= row) ++own;
-    crow[idx] = (own << 24) | (row - rows_s[own]);
-    if (P.cl_w_smem) w32c[idx] = P.wcm32[static_cast<int64_t>(l) * N + m0 + i];
-  }
-  double part = 0.0;
-  for (int i = tid; i < nm; i += T) {
-    const double g = P.sp[m0 + i].x;
-    g64[i] = g;
-    x64[i] = 0.0;
-    part += g * g;
-  }
-  cl.sync();  // every block's slices are in place before any remote read
-  const double gamma0 = cl_sum_d(c, part);
-  int status = FCT_OK, iters = 0, refines = 0;
-  double gfinal = gamma0;
-  if (!isfinite(gamma0)) {
-    status = FCT_ERR_NONFINITE;
-  } else if (gamma0 > 0.0) {
-    const double cs = sqrt(gamma0), ci = 1.0 / cs;
-    double g_cur = gamma0;
-    for (int k = 0;; ++k) {
-      for (int i = tid; i < nm; i += T) {
-        sp32[i] = make_float2(static_cast<float>(g64[i] * ci), 0.0f);
-        dx32[i] = 0.0f;
-      }
-      cl.sync();
-      ++refines;
-      int it_in = 0;
-      double g_in = 0.0;
-      const int st_in = P.cl_w_smem
-                            ? cluster_cgne<float, true>(c, dx32, g_cur * ci * ci, a.inner_tol, a.max_iter, 64, &it_in, &g_in)
-                            : cluster_cgne<float, false>(c, dx32, g_cur * ci * ci, a.inner_tol, a.max_iter, 64, &it_in,
-                                                         &g_in);
-      iters += it_in;
-      if (st_in == FCT_ERR_NONFINITE) {
-        status = st_in;
-        break;
-      }
-      for (int i = tid; i < nm; i += T) x64[i] = fma(cs, static_cast<double>(dx32[i]), x64[i]);
-      cl.sync();
-      // r = b - A x (FP64)
-      for (int r = tid; r < nr; r += T) {
-        double ax = 0.0;
-        for (int j = rowptr[r]; j < rowptr[r + 1]; ++j) ax = fma(__ldg(P.wcsr + e0 + j), cl_remote<double>(c, L.x64, col[j]), ax);
-        qr[r] = P.b[r0 + r] - ax;
-      }
-      cl.sync();
-      // g = A^T r (FP64)
-      part = 0.0;
-      for (int i = tid; i < nm; i += T) {
-        double t = 0.0;
-        for (int l = 0; l < K; ++l)
-          t = fma(__ldg(P.wcm + static_cast<int64_t>(l) * N + m0 + i), cl_remote<double>(c, L.qr, crow[l * nm + i]), t);
-        g64[i] = t;
-        part += t * t;
-      }
-      const double g_prev = g_cur;
-      g_cur = cl_sum_d(c, part);
-      gfinal = g_cur;
-      if (!isfinite(g_cur)) {
-        status = FCT_ERR_NONFINITE;
-        break;
-      }
-      if (!(g_cur > 0.0) || g_cur <= a.tol * a.tol * gamma0) break;
-      if (k + 1 >= a.max_refine || g_cur > 1e-2 * g_prev) {
-        // FP32 inner solves no longer gain a digit per sweep: finish in FP64
-        // from the current x, starting from this sweep's exact g.
-        for (int i = tid; i < nm; i += T) sp64[i] = make_double2(g64[i], 0.0);
-        cl.sync();
-        int it64 = 0;
-        double g_out = g_cur;
-        const double tol_eff = a.tol * sqrt(gamma0 / g_cur);
-        status = cluster_cgne<double, false>(c, x64, g_cur, tol_eff, a.max_iter, 0, &it64, &g_out);
-        iters += it64;
-        gfinal = g_out;
-        break;
-      }
-    }
-  }
-  for (int i = tid; i < nm; i += T) a.coeffs[m0 + i] = x64[i];
-  if (rank == 0 && tid == 0) {
-    fct_report rep;
-    rep.status = status;
-    rep.iterations = iters;
-    rep.refinements = refines;
-    rep.reserved = 0;
-    rep.rel_normal_residual = gamma0 > 0.0 ? sqrt(gfinal / gamma0) : 0.0;
-    rep.gamma0 = gamma0;
-    *a.report = rep;
-  }
-  cl.sync();  // no block leaves while another may still read its shared memory
-}
 
 // ---------------------------------------------------------------------------
 // Sampler (workload generator, "sample f" of Algorithm 3)
@@ -662,7 +283,6 @@ struct fct_plan_s {
   int smem_cap = 0;            // largest request that keeps blocks_per_sm resident
   std::vector<int32_t> ru_first, rowptr_h;  // for the shared-memory sizing of other team sizes
   std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
-  int cl_smem = 0;                          // dynamic shared memory per block of the cluster solver
   bool stage_values = false;                // single launches stage the CG loop's entry values too
   double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
@@ -799,108 +419,6 @@ fct_status choose_shape(fct_plan P) {
                                                            P->block_threads, P->smem_bytes));
     if (chk * prop.multiProcessorCount < P->grid_blocks) P->stage_values = false;
   }
-  return FCT_OK;
-}
-
-// Cluster solver set-up (mixed path, option cluster_solve): split the rows by
-// entry count and the coefficients in equal chunks over a cluster of 16
-// blocks (8 when 16 cannot be scheduled), and keep it only if every block's
-// slice fits in shared memory.  Leaves hp.cl_cs = 0 when it does not fit.
-fct_status setup_cluster(fct_plan P) {
-  DevPlan& hp = P->hp;
-  hp.cl_cs = 0;
-  int dev = 0, optin = 0;
-  FCT_CUDA(cudaGetDevice(&dev));
-  FCT_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  cudaFuncAttributes fa;
-  FCT_CUDA(cudaFuncGetAttributes(&fa, cluster_solve_kernel));
-  const int cap = optin - static_cast<int>(fa.sharedSizeBytes);
-  const int64_t R = P->R, N = P->N, K = P->K;
-  const std::vector<int32_t>& rp = P->rowptr_h;
-  const int64_t nnz = rp[R];
-  if (N < 1 || R < 1) return FCT_OK;
-  for (int CS : {16, 8}) {
-    if (N < CS || R < CS) continue;
-    std::vector<int32_t> rows(CS + 1, 0);
-    for (int c = 1; c < CS; ++c) {
-      const int64_t target = nnz * c / CS;
-      int64_t r = rows[c - 1];
-      while (r < R && rp[r] < target) ++r;
-      rows[c] = static_cast<int32_t>(r);
-    }
-    rows[CS] = static_cast<int32_t>(R);
-    const int nc = static_cast<int>((N + CS - 1) / CS);
-    if (nc >= (1 << 24)) continue;
-    int maxrows = 0;
-    for (int c = 0; c < CS; ++c) maxrows = std::max(maxrows, rows[c + 1] - rows[c]);
-    if (maxrows >= (1 << 24)) continue;
-    int wsmem = -1, need = 0;
-    for (int ws : {1, 0}) {
-      int nd = 0;
-      for (int c = 0; c < CS; ++c) {
-        const int nr = rows[c + 1] - rows[c], ne = rp[rows[c + 1]] - rp[rows[c]];
-        const int nm = static_cast<int>(std::max<int64_t>(0, std::min<int64_t>(N, int64_t{c + 1} * nc) - int64_t{c} * nc));
-        nd = std::max(nd, cluster_layout(nc, maxrows, nr, ne, nm, static_cast<int>(K), ws).end);
-      }
-      if (nd <= cap) {
-        wsmem = ws;
-        need = nd;
-        break;
-      }
-    }
-    if (wsmem < 0) continue;
-    if (CS > 8) FCT_CUDA(cudaFuncSetAttribute(cluster_solve_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    FCT_CUDA(cudaFuncSetAttribute(cluster_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, need));
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CS);
-    cfg.blockDim = dim3(kClusterThreads);
-    cfg.dynamicSmemBytes = static_cast<size_t>(need);
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = CS;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, cluster_solve_kernel, &cfg) != cudaSuccess || nclusters < 1) {
-      (void)cudaGetLastError();
-      continue;
-    }
-    FCT_CUDA(cudaMemcpy(const_cast<int32_t*>(hp.cl_rows), rows.data(), sizeof(int32_t) * (CS + 1),
-                        cudaMemcpyHostToDevice));
-    hp.cl_cs = CS;
-    hp.cl_nc = nc;
-    hp.cl_maxrows = maxrows;
-    hp.cl_w_smem = wsmem;
-    P->cl_smem = need;
-    return FCT_OK;
-  }
-  return FCT_OK;
-}
-
-fct_status launch_cluster(fct_plan P, double* coeffs, cudaStream_t st) {
-  ClusterArgs ca{};
-  ca.plan = P->dp;
-  ca.coeffs = coeffs;
-  ca.report = P->drep;
-  ca.tol = P->opt.tol;
-  ca.inner_tol = P->opt.inner_tol;
-  ca.max_iter = P->opt.max_iter;
-  ca.max_refine = P->opt.max_refine;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(P->hp.cl_cs);
-  cfg.blockDim = dim3(kClusterThreads);
-  cfg.dynamicSmemBytes = static_cast<size_t>(P->cl_smem);
-  cfg.stream = st;
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = P->hp.cl_cs;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  FCT_CUDA(cudaLaunchKernelEx(&cfg, cluster_solve_kernel, ca));
   return FCT_OK;
 }
 
@@ -1041,7 +559,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     const int64_t KN2 = 2 * static_cast<int64_t>(K) * N;
     const int64_t bound = normal_matrix_bound(H);
     bool want = o.normal_matrix > 0 ||
-                (o.normal_matrix == 0 && o.cluster_solve <= 0 && o.precision == FCT_MIXED && bound <= 2 * KN2);
+                (o.normal_matrix == 0 && o.precision == FCT_MIXED && bound <= 2 * KN2);
     if (o.normal_matrix > 0 && bound > (int64_t{1} << 30)) {
       delete P;
       return fail(FCT_ERR_INVALID_ARG, "normal_matrix = 1 but A^T A would exceed 2^30 nonzeros");
@@ -1114,9 +632,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&d_crow, sizeof(int32_t) * KN);
   add(&d_wcm, sizeof(double) * KN);
   add(&d_wcm32, sizeof(float) * KN);
-  int32_t *d_wrowptr, *d_wcol, *d_cl_rows;
+  int32_t *d_wrowptr, *d_wcol;
   float* d_wval;
-  add(&d_cl_rows, sizeof(int32_t) * (kMaxCluster + 1));
   add(&d_wrowptr, sizeof(int32_t) * (nnzw > 0 ? N + 1 : 1));
   add(&d_wcol, sizeof(int32_t) * nnzw);
   add(&d_wval, sizeof(float) * nnzw);
@@ -1128,13 +645,11 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   add(&hp.sp, sizeof(double2) * N);
   add(&hp.part_r, sizeof(double) * hp.n_row_units);
   add(&hp.part_c, sizeof(double) * hp.n_coef_chunks);
-  add(&hp.pr32, sizeof(float) * hp.n_row_units);
-  add(&hp.pc32, sizeof(float) * hp.n_coef_chunks);
   add(&hp.q32, sizeof(float) * H.R);
   add(&hp.sp32, sizeof(float2) * N);
   add(&hp.dx32, sizeof(float) * N);
   add(&hp.wv, sizeof(float) * (hp.n_w_units > 0 ? 6 * N : 1));
-  add(&hp.pw32, sizeof(float2) * 2 * std::max(hp.n_w_units, 1));
+  add(&hp.pw64, sizeof(double2) * 2 * std::max(hp.n_w_units, 1));
   add(&P->d_sizes, sizeof(int32_t) * K * D);
   add(&P->d_offsets, sizeof(int64_t) * (K + 1));
   add(&P->d_node_off, sizeof(int32_t) * K * D);
@@ -1176,7 +691,6 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.wcm = d_wcm;
   hp.wcm32 = d_wcm32;
   hp.wrowptr = d_wrowptr;
-  hp.cl_rows = d_cl_rows;
   hp.wcol = d_wcol;
   hp.wval = d_wval;
 
@@ -1231,8 +745,6 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(P->d_emats, H.eval_mats.data(), sizeof(double) * H.eval_mats.size()));
   s = FCT_OK;
   if (ue == cudaSuccess) s = choose_shape(P);
-  if (ue == cudaSuccess && s == FCT_OK && o.cluster_solve > 0 && o.precision == FCT_MIXED && hp.n_w_units == 0)
-    s = setup_cluster(P);
   if (ue == cudaSuccess && s == FCT_OK) chk(up(P->dp, &hp, sizeof(DevPlan)));
   if (ue == cudaSuccess && s == FCT_OK && nnodes > 0) {
     cheb_table_kernel<<<static_cast<unsigned>((nnodes + 127) / 128), 128>>>(P->d_node_pos, static_cast<int>(nnodes),
@@ -1288,7 +800,6 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->coef_lanes = P->hp.coef_lanes;
   info->device_bytes = static_cast<int64_t>(P->dbytes);
   info->normal_nnz = P->hp.n_w_units > 0 ? static_cast<int64_t>(P->w_rowptr_h.back()) : 0;
-  info->cluster_blocks = P->hp.cl_cs;
   return FCT_OK;
 }
 
@@ -1416,14 +927,8 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
   a.ls = P->ls;
   a.timeout_ns = timeout_ns(P);
   a.smem_bytes = P->smem_bytes;
-  const bool cluster = P->hp.cl_cs > 0 && P->opt.precision == FCT_MIXED;
-  if (cluster) a.single.flags = kJobPrepareOnly;  // the team kernel forms b and A^T b
   fct_status s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
   if (s != FCT_OK) return s;
-  if (cluster) {
-    s = launch_cluster(P, coeffs, st);
-    if (s != FCT_OK) return s;
-  }
   if (rep) return read_report(P, P->drep, st, rep);
   return FCT_OK;
 }
@@ -1606,7 +1111,6 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
   C->ru_first = src->ru_first;
   C->rowptr_h = src->rowptr_h;
   C->w_rowptr_h = src->w_rowptr_h;
-  C->cl_smem = src->cl_smem;
   // its own workspace, DevPlan copy, launch state and report
   DevPlan& hp = C->hp;
   const size_t M = static_cast<size_t>(std::max<int64_t>(C->M, 1)), R = static_cast<size_t>(C->R),
@@ -1627,13 +1131,11 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
       {reinterpret_cast<void**>(&hp.sp), sizeof(double2) * N},
       {reinterpret_cast<void**>(&hp.part_r), sizeof(double) * hp.n_row_units},
       {reinterpret_cast<void**>(&hp.part_c), sizeof(double) * hp.n_coef_chunks},
-      {reinterpret_cast<void**>(&hp.pr32), sizeof(float) * hp.n_row_units},
-      {reinterpret_cast<void**>(&hp.pc32), sizeof(float) * hp.n_coef_chunks},
       {reinterpret_cast<void**>(&hp.q32), sizeof(float) * R},
       {reinterpret_cast<void**>(&hp.sp32), sizeof(float2) * N},
       {reinterpret_cast<void**>(&hp.dx32), sizeof(float) * N},
       {reinterpret_cast<void**>(&hp.wv), sizeof(float) * (hp.n_w_units > 0 ? 6 * N : 1)},
-      {reinterpret_cast<void**>(&hp.pw32), sizeof(float2) * 2 * std::max(hp.n_w_units, 1)},
+      {reinterpret_cast<void**>(&hp.pw64), sizeof(double2) * 2 * std::max(hp.n_w_units, 1)},
   };
   size_t total = 0;
   for (auto& pc : pieces) total += align256(std::max<size_t>(pc.bytes, 1));
@@ -1680,9 +1182,15 @@ constexpr int kNoallocMaxDevices = 64;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};  // device address of the array, per device
 std::mutex g_noalloc_mu;
 
+// Writes the call's DevPlan into the array from a kernel argument, so no host
+// buffer has to outlive the call.
+__global__ void noalloc_put_plan_kernel(DevPlan* dst, const DevPlan src) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = src;
+}
+
 // Layout of the workspace inside the array (256-byte aligned pieces).
 struct NoallocLayout {
-  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, pr32, pc32, q32, sp32, dx32, wv, pw32, total;
+  size_t devplan, report, ls, y0, y1, b, rres, q, sp, part_r, part_c, q32, sp32, dx32, wv, pw64, total;
 };
 
 NoallocLayout noalloc_layout(const fct_plan P) {
@@ -1706,13 +1214,11 @@ NoallocLayout noalloc_layout(const fct_plan P) {
   L.sp = take(sizeof(double2) * N);
   L.part_r = take(sizeof(double) * P->hp.n_row_units);
   L.part_c = take(sizeof(double) * P->hp.n_coef_chunks);
-  L.pr32 = take(sizeof(float) * P->hp.n_row_units);
-  L.pc32 = take(sizeof(float) * P->hp.n_coef_chunks);
   L.q32 = take(sizeof(float) * R);
   L.sp32 = take(sizeof(float2) * N);
   L.dx32 = take(sizeof(float) * N);
   L.wv = take(sizeof(float) * (P->hp.n_w_units > 0 ? 6 * N : 1));
-  L.pw32 = take(sizeof(float2) * 2 * std::max(P->hp.n_w_units, 1));
+  L.pw64 = take(sizeof(double2) * 2 * std::max(P->hp.n_w_units, 1));
   L.total = off;
   return L;
 }
@@ -1756,13 +1262,11 @@ extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, dou
   hp.sp = reinterpret_cast<double2*>(b + L.sp);
   hp.part_r = reinterpret_cast<double*>(b + L.part_r);
   hp.part_c = reinterpret_cast<double*>(b + L.part_c);
-  hp.pr32 = reinterpret_cast<float*>(b + L.pr32);
-  hp.pc32 = reinterpret_cast<float*>(b + L.pc32);
   hp.q32 = reinterpret_cast<float*>(b + L.q32);
   hp.sp32 = reinterpret_cast<float2*>(b + L.sp32);
   hp.dx32 = reinterpret_cast<float*>(b + L.dx32);
   hp.wv = reinterpret_cast<float*>(b + L.wv);
-  hp.pw32 = reinterpret_cast<float2*>(b + L.pw32);
+  hp.pw64 = reinterpret_cast<double2*>(b + L.pw64);
   DevPlan* dplan = reinterpret_cast<DevPlan*>(b + L.devplan);
   fct_report* drep = reinterpret_cast<fct_report*>(b + L.report);
   LaunchState* ls = reinterpret_cast<LaunchState*>(b + L.ls);
@@ -1770,7 +1274,8 @@ extern "C" fct_status fct_execute_noalloc(fct_plan P, const double* samples, dou
   // team's barrier counters must start at zero.
   FCT_CUDA(cudaMemsetAsync(ls, 0, offsetof(LaunchState, team_job), st));
   FCT_CUDA(cudaMemsetAsync(&ls->bars[0], 0, sizeof(TeamBarrier), st));
-  FCT_CUDA(cudaMemcpyAsync(dplan, &hp, sizeof(DevPlan), cudaMemcpyHostToDevice, st));
+  noalloc_put_plan_kernel<<<1, 32, 0, st>>>(dplan, hp);
+  FCT_CUDA(cudaGetLastError());
   SolveArgs a{};
   a.single = make_job(P, samples, coeffs, drep);
   a.single.plan = dplan;
@@ -1925,6 +1430,9 @@ struct fct_server_s {
 namespace {
 
 fct_status server_ensure_running(fct_server S) {
+  const int derr = __atomic_load_n(&S->h_ring->err, __ATOMIC_ACQUIRE);
+  if (derr != 0)
+    return fail(static_cast<fct_status>(derr), "the serving launch abandoned its jobs after a device-side error");
   if (S->launched && cudaEventQuery(S->done_ev) == cudaErrorNotReady) return FCT_OK;
   if (S->launched) {
     int err = 0;
@@ -2034,7 +1542,9 @@ fct_status fct_server_poll(fct_server S, int64_t ticket, int* done, fct_report* 
     if (rep) *rep = slot.rep;
     return FCT_OK;
   }
-  // a job published just as the launch went idle is picked up by a new launch
+  // not finished: a device-side error published by the running launch ends
+  // the wait here (the job will never be solved); otherwise a job published
+  // just as the launch went idle is picked up by a new launch
   return server_ensure_running(S);
 }
 
@@ -2127,24 +1637,24 @@ extern "C" fct_status fct_plan_condition(fct_plan P, const double* start, double
       P->d_hist_block = nullptr;
       P->hist_cap = 0;
     }
-    FCT_CUDA(cudaMalloc(&P->d_hist_block, align256(sizeof(DevPlan)) + sizeof(float2) * iterations));
+    FCT_CUDA(cudaMalloc(&P->d_hist_block, align256(sizeof(DevPlan)) + sizeof(double2) * iterations));
     P->hist_cap = iterations;
   }
   DevPlan hp = P->hp;
   hp.s_init = start;
-  hp.hist = reinterpret_cast<float2*>(P->d_hist_block + align256(sizeof(DevPlan)));
+  hp.hist = reinterpret_cast<double2*>(P->d_hist_block + align256(sizeof(DevPlan)));
   hp.hist_cap = iterations;
   DevPlan* dplan = reinterpret_cast<DevPlan*>(P->d_hist_block);
   FCT_CUDA(cudaMemcpyAsync(dplan, &hp, sizeof(DevPlan), cudaMemcpyHostToDevice, st));
-  FCT_CUDA(cudaMemsetAsync(hp.hist, 0, sizeof(float2) * iterations, st));
+  FCT_CUDA(cudaMemsetAsync(hp.hist, 0, sizeof(double2) * iterations, st));
   SolveArgs a{};
   a.single = make_job(P, nullptr, work, P->drep);
   a.single.plan = dplan;
   a.single.precision = FCT_FP64;
   a.single.max_iter = iterations;
   // Stop once the normal residual has fallen by 1e12: the extreme Ritz values
-  // have converged by then, and further iterations would take alpha and beta
-  // from relative squares below FP32's normal range, where they lose precision.
+  // have converged by then, and the CG coefficients of a nearly converged
+  // iteration carry mostly rounding.
   a.single.tol = 1e-12;
   a.jobs = nullptr;
   a.njobs = 1;
@@ -2157,11 +1667,11 @@ extern "C" fct_status fct_plan_condition(fct_plan P, const double* start, double
   fct_report rep;
   s = read_report(P, P->drep, st, &rep);
   if (s != FCT_OK && s != FCT_ERR_NOCONV) return s;
-  std::vector<float2> h(iterations);
-  FCT_CUDA(cudaMemcpy(h.data(), hp.hist, sizeof(float2) * iterations, cudaMemcpyDeviceToHost));
+  std::vector<double2> h(iterations);
+  FCT_CUDA(cudaMemcpy(h.data(), hp.hist, sizeof(double2) * iterations, cudaMemcpyDeviceToHost));
   int k = std::min(rep.iterations, iterations);
   for (int j = 0; j < k; ++j)
-    if (!(h[j].x > 0.0f) || !std::isfinite(h[j].x) || !(h[j].y >= 0.0f) || !std::isfinite(h[j].y)) {
+    if (!(h[j].x > 0.0) || !std::isfinite(h[j].x) || !(h[j].y >= 0.0) || !std::isfinite(h[j].y)) {
       k = j;
       break;
     }
@@ -2169,8 +1679,8 @@ extern "C" fct_status fct_plan_condition(fct_plan P, const double* start, double
   std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
   for (int j = 0; j < k; ++j) {
     const double al = h[j].x;
-    d[j] = 1.0 / al + (j > 0 ? static_cast<double>(h[j].y) / static_cast<double>(h[j - 1].x) : 0.0);
-    if (j + 1 < k) e[j] = std::sqrt(static_cast<double>(h[j + 1].y)) / al;
+    d[j] = 1.0 / al + (j > 0 ? h[j].y / h[j - 1].x : 0.0);
+    if (j + 1 < k) e[j] = std::sqrt(h[j + 1].y) / al;
   }
   double lmin = 0.0, lmax = 0.0;
   tridiag_extremes(d, e, &lmin, &lmax);

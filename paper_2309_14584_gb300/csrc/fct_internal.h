@@ -84,10 +84,8 @@ struct DevPlan {
   double* rres;              // [R] FP64 residual b - A x (mixed path sweeps)
   double* q;                 // [R]
   double2* sp;               // [N] {s, p} interleaved: one 16-byte gather per entry
-  double* part_r;            // [n_row_units]    FP64 partials (set-up and refinement phases)
-  double* part_c;            // [n_coef_chunks]
-  float* pr32;               // [n_row_units]    FP32 partials of the CG loop (relative |q|^2)
-  float* pc32;               // [n_coef_chunks]  (relative |s|^2)
+  double* part_r;            // [n_row_units]    FP64 per-unit partial sums (|q|^2 and the set-up phases)
+  double* part_c;            // [n_coef_chunks]  (|s|^2 and the refinement sweeps)
   // FP32 workspace of the mixed path
   float* q32;                // [R]
   float2* sp32;              // [N] {s, p} of the inner FP32 solve
@@ -102,20 +100,12 @@ struct DevPlan {
   int32_t w_rows_per_unit;   // = workers / w_lanes
   int32_t pad_w;
   float* wv;                 // [6N] w (two buffers), r, p, s, z of the pipelined CG
-  float2* pw32;              // [2 * n_w_units] partial (r.r, w.r), two buffers
-  // cluster solver of the mixed path (cl_cs = 0: not set up): one thread-block
-  // cluster holds the FP32 tables and the Krylov vectors in distributed shared
-  // memory; rows are split by entry count, coefficients in chunks of cl_nc
-  const int32_t* cl_rows;    // [cl_cs + 1] first row of every block of the cluster
-  int32_t cl_cs;             // blocks per cluster
-  int32_t cl_nc;             // coefficients per block
-  int32_t cl_maxrows;        // most rows of one block
-  int32_t cl_w_smem;         // 1: FP32 entry values staged in shared memory too
+  double2* pw64;             // [2 * n_w_units] FP64 partials (r.r, w.r), two buffers
   // condition estimate: when set, the FP64 solve starts from s = s_init (no
   // DCT, no b) and block 0 records (alpha_k, beta_k) of every CG iteration,
   // the Lanczos coefficients of A^T A for the start vector s_init
   const double* s_init;      // [N] or nullptr
-  float2* hist;              // [hist_cap] or nullptr
+  double2* hist;             // [hist_cap] (alpha_k, beta_k) or nullptr
   int32_t hist_cap;
   int32_t pad_hist;
 };
@@ -129,7 +119,7 @@ struct SolveJob {
   int32_t precision;
   int32_t max_iter;
   int32_t max_refine;
-  int32_t flags;             // kJobPrepareOnly: stop after s = A^T b (the cluster solver continues)
+  int32_t flags;             // kJobPrepareOnly: stop after b and s = A^T b (the DCT stage alone)
   double tol;
   double inner_tol;
 };
@@ -178,7 +168,8 @@ struct ServerSlot {
 struct ServerRing {
   unsigned long long tail;  // jobs published so far (monotonic)
   int stop;                 // host asks the serving kernel to leave
-  int pad[13];
+  int err;                  // device: the launch's error code once a team abandoned its job
+  int pad[12];
   ServerSlot slots[kRingSize];
 };
 

@@ -560,7 +560,6 @@ void fct_default_options(fct_options* opt) {
   opt->normal_matrix = 0;
   opt->grid_kind = FCT_GRID_EXTREMA;
   opt->entries_per_lane = 0;
-  opt->cluster_solve = 0;
   opt->plan_build = FCT_PLAN_BUILD_AUTO;
 }
 

@@ -432,12 +432,11 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
 // unit's partial is the fixed-order sum of its warps' sums, so partials (and
 // the result) do not depend on the team size.
 //
-// GB300 executes FP64 at a small fraction of its FP32 rate, so only the
-// vector arithmetic that needs it runs in V: the sums of squares that give
-// alpha and beta are taken relative to gamma0 and reduced in FP32 (fixed
-// order), and alpha, beta and the stopping test are computed once per block
-// by one thread and broadcast.  With V = float (the inner solve of the mixed
-// path) the loop does no FP64 arithmetic at all.
+// The inner products that give alpha and beta (|q|^2, |s|^2) are always
+// formed and reduced in FP64, also when the vectors are FP32 (V = float, the
+// inner solve of the mixed path): each owner squares its value in FP64, and
+// the per-unit partials are summed in a fixed order.  alpha, beta and the
+// stopping test are computed once per block by one thread and broadcast.
 // On entry sp[m].x = right-hand side, x = 0, gamma0 = |s|^2 (> 0).  Stops when
 // gamma <= tol^2 gamma0, after max_iter (FCT_ERR_NOCONV) or, if stall > 0,
 // when gamma has not decreased for `stall` iterations.  All threads of all
@@ -452,8 +451,8 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
                           int* iters_out, double* gamma_out, int* status_out, double* red) {
   using V2 = typename Vec2<V>::T;
   constexpr int NW = BT / 32 - 1;  // worker warps
-  __shared__ float wpart[kUnitGroup][NW];
-  __shared__ float sh_ab[2];       // beta, alpha
+  __shared__ double wpart[kUnitGroup][NW];
+  __shared__ double sh_ab[2];      // beta, alpha
   __shared__ int sh_ctl[3];        // stop flag, status, iterations
   *status_out = FCT_OK;
   *iters_out = 0;
@@ -466,24 +465,24 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   const int wk = static_cast<int>(threadIdx.x) - 32;  // worker index; warp 0 has wk < 0
   const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
   const int lane32 = threadIdx.x & 31;
-  const V rs = static_cast<V>(1.0 / sqrt(gamma0));   // squares are taken relative to gamma0
-  const float tol2 = static_cast<float>(tol * tol);
+  const double rs = 1.0 / sqrt(gamma0);   // squares are taken relative to gamma0
+  const double tol2 = tol * tol;
   // thread 0's state (relative gamma)
-  float gam = 1.0f, best = 1.0f;
+  double gam = 1.0, best = 1.0;
   int it = 0, best_it = 0;
   bool first = true;
   auto relsq = [&](V v) {
-    const float t = static_cast<float>(v * rs);
+    const double t = static_cast<double>(v) * rs;
     return t * t;
   };
-  auto warp_part = [&](int kk, float v) {
+  auto warp_part = [&](int kk, double v) {
     v = warp_sum(v);
     if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
   };
-  auto flush = [&](float* part, int u0, int nk) {
+  auto flush = [&](double* part, int u0, int nk) {
     __syncthreads();
     if (threadIdx.x < nk) {
-      float v = 0.0f;
+      double v = 0.0;
 #pragma unroll
       for (int w2 = 0; w2 < NW; ++w2) v += wpart[threadIdx.x][w2];
       stcg(part + u0 + threadIdx.x * tm.G, v);
@@ -504,11 +503,11 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       if (wk >= 0) {
         if (u < nru) gather_a(u, 0, &as, &ap, &row, &lead);
       } else {
-        float gnew = 1.0f;
-        if (!first) gnew = warp0_team_sum_f(P.pc32, ncc);
+        double gnew = 1.0;
+        if (!first) gnew = warp0_sum(P.part_c, ncc);
         if (threadIdx.x == 0) {
           int c = 0;
-          float bt = 0.0f;
+          double bt = 0.0;
           if (!first) {
             ++it;
             if (!isfinite(gnew)) {
@@ -540,7 +539,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       for (; u < nru; u += tm.G, ++k) {
         if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
         if (u < nwide) wide_row_combine<NW>(wk, &as, &ap, &lead);
-        float part = 0.0f;
+        double part = 0.0;
         if (wk >= 0 && lead) {
           const V qv = first ? as : fma(beta, ap, as);
           stcg(q + row, qv);
@@ -548,12 +547,12 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && u + tm.G < nru) {
-          flush(P.pr32, u0, kg);
+          flush(P.part_r, u0, kg);
           kg = 0;
           u0 = u + tm.G;
         }
       }
-      if (!phase_end<NW>(tm, wpart, P.pr32, u0, kg)) return false;
+      if (!phase_end<NW>(tm, wpart, P.part_r, u0, kg)) return false;
     }
     // ================= phase B: t = A^T q; {s, p} and x updated by the owner
     {
@@ -577,17 +576,17 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           t = coef_gather<V, WT, SV>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
         }
       } else {
-        const float dl = warp0_team_sum_f(P.pr32, nru);
+        const double dl = warp0_sum(P.part_r, nru);
         if (threadIdx.x == 0) {
           int cc = 0;
-          float al = 0.0f;
+          double al = 0.0;
           if (!isfinite(dl)) cc = FCT_ERR_NONFINITE + 16;
-          else if (!(dl > 0.0f)) cc = 1;  // q = 0: s is already zero to working precision
+          else if (!(dl > 0.0)) cc = 1;  // q = 0: s is already zero to working precision
           else al = gam / dl;
           sh_ab[1] = al;
           sh_ctl[0] = cc;
           if (P.hist != nullptr && tm.rank == 0 && cc == 0 && pass < P.hist_cap)
-            P.hist[pass] = make_float2(al, first ? 0.0f : sh_ab[0]);
+            P.hist[pass] = make_double2(al, first ? 0.0 : sh_ab[0]);
         }
       }
       __syncthreads();
@@ -601,7 +600,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           own_load(c, &o, &xo);
           t = coef_gather<V, WT, SV>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
-        float part = 0.0f;
+        double part = 0.0;
         if (wk >= 0 && lead) {
           const V pn = first ? o.x : fma(beta, o.y, o.x);
           const V sn = fma(-alpha, t, o.x);
@@ -614,12 +613,12 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && c + tm.G < ncc) {
-          flush(P.pc32, c0, kg);
+          flush(P.part_c, c0, kg);
           kg = 0;
           c0 = c + tm.G;
         }
       }
-      if (!phase_end<NW>(tm, wpart, P.pc32, c0, kg)) return false;
+      if (!phase_end<NW>(tm, wpart, P.part_c, c0, kg)) return false;
     }
     first = false;
   }
@@ -632,7 +631,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   __syncthreads();
   *status_out = sh_ctl[1];
   *iters_out = sh_ctl[2];
-  *gamma_out = static_cast<double>(sh_ab[0]) * gamma0;
+  *gamma_out = sh_ab[0] * gamma0;
   __syncthreads();
   return true;
 }
@@ -658,8 +657,8 @@ template <int BT>
 __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, double gamma0, double tol, int max_iter,
                              int stall, int* iters_out, double* gamma_out, int* status_out) {
   constexpr int NW = BT / 32 - 1;
-  __shared__ float2 wpart2[kUnitGroup][NW];
-  __shared__ float sh_ab[3];   // alpha, beta, final relative gamma
+  __shared__ double2 wpart2[kUnitGroup][NW];
+  __shared__ double sh_ab[3];  // alpha, beta, final relative gamma
   __shared__ int sh_ctl[2];    // stop flag, iterations
   *status_out = FCT_OK;
   *iters_out = 0;
@@ -672,8 +671,8 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
   const int wk = static_cast<int>(threadIdx.x) - 32;
   const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
   const int lane32 = threadIdx.x & 31;
-  const float rs = static_cast<float>(1.0 / sqrt(gamma0));
-  const float tol2 = static_cast<float>(tol * tol);
+  const double rs = 1.0 / sqrt(gamma0);
+  const double tol2 = tol * tol;
   float* const wb0 = P.wv;
   float* const wb1 = P.wv + N;
   float* const vr = P.wv + 2 * static_cast<size_t>(N);
@@ -683,7 +682,7 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
   float* const vx = P.dx32;
   const float* const rhs = reinterpret_cast<const float*>(P.sp32);  // .x of {s, p}: stride 2
   // thread 0's state
-  float gam_prev = 1.0f, al_prev = 1.0f, best = 3.0e38f, gam_last = 1.0f;
+  double gam_prev = 1.0, al_prev = 1.0, best = 1.0e300, gam_last = 1.0;
   int best_it = 0;
 
   // y[m] = sum_j W[m][j] src[j * stride] for row m of unit u (k-th unit of this block)
@@ -724,15 +723,15 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
     }
     return lane_group_sum((a0 + a1) + (a2 + a3), LW);
   };
-  auto warp_part2 = [&](int kk, float2 v) {
+  auto warp_part2 = [&](int kk, double2 v) {
     v.x = warp_sum(v.x);
     v.y = warp_sum(v.y);
     if (wk >= 0 && lane32 == 0) wpart2[kk][warp] = v;
   };
-  auto flush2 = [&](float2* part, int u0, int nk) {
+  auto flush2 = [&](double2* part, int u0, int nk) {
     __syncthreads();
     if (threadIdx.x < nk) {
-      float2 v = make_float2(0.0f, 0.0f);
+      double2 v = make_double2(0.0, 0.0);
 #pragma unroll
       for (int w2 = 0; w2 < NW; ++w2) v = padd(v, wpart2[threadIdx.x][w2]);
       stcg(part + u0 + threadIdx.x * tm.G, v);
@@ -748,30 +747,30 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
       bool lead = false;
       float y = 0.0f;
       if (wk >= 0) y = gather(u, k, rhs, 2, &m, &lead);
-      float2 part = make_float2(0.0f, 0.0f);
+      double2 part = make_double2(0.0, 0.0);
       if (wk >= 0 && lead) {
         const float r = ldcg(rhs + 2 * static_cast<size_t>(m));
         stcg(vr + m, r);
         stcg(wb0 + m, y);
         stcg(vx + m, 0.0f);
-        const float tr = r * rs, tw = y * rs;
-        part = make_float2(tr * tr, tw * tr);
+        const double tr = r * rs, tw = y * rs;
+        part = make_double2(tr * tr, tw * tr);
       }
       warp_part2(kg, part);
       if (++kg == kUnitGroup && u + tm.G < nwu) {
-        flush2(P.pw32, u0, kg);
+        flush2(P.pw64, u0, kg);
         kg = 0;
         u0 = u + tm.G;
       }
     }
-    if (!phase_end<NW>(tm, wpart2, P.pw32, u0, kg)) return false;
+    if (!phase_end<NW>(tm, wpart2, P.pw64, u0, kg)) return false;
   }
   int ctl = 0, it = 0;
   for (;; ++it) {
     const float* wcur = (it & 1) ? wb1 : wb0;
     float* wnext = (it & 1) ? wb0 : wb1;
-    const float2* pin = P.pw32 + ((it & 1) ? nwu : 0);
-    float2* pout = P.pw32 + ((it & 1) ? 0 : nwu);
+    const double2* pin = P.pw64 + ((it & 1) ? nwu : 0);
+    double2* pout = P.pw64 + ((it & 1) ? 0 : nwu);
     int u = tm.rank;
     int m = 0;
     bool lead = false;
@@ -792,11 +791,11 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
         if (lead) own_load();
       }
     } else {
-      const float2 g = warp0_team_sum_f2(pin, nwu);
+      const double2 g = warp0_sum(pin, nwu);
       if (threadIdx.x == 0) {
         int c = 0;
-        float al = 0.0f, bt = 0.0f;
-        const float gam = g.x, del = g.y;
+        double al = 0.0, bt = 0.0;
+        const double gam = g.x, del = g.y;
         gam_last = gam;
         if (!isfinite(gam) || !isfinite(del)) {
           c = FCT_ERR_NONFINITE + 16;
@@ -814,9 +813,9 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
             }
           }
           if (c == 0) {
-            bt = it == 0 ? 0.0f : gam / gam_prev;
-            const float den = it == 0 ? del : del - bt * gam / al_prev;
-            if (!(den > 0.0f)) {
+            bt = it == 0 ? 0.0 : gam / gam_prev;
+            const double den = it == 0 ? del : del - bt * gam / al_prev;
+            if (!(den > 0.0)) {
               c = 1;  // W is positive semidefinite: no further progress in this precision
             } else {
               al = gam / den;
@@ -833,14 +832,14 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
     __syncthreads();
     ctl = sh_ctl[0];
     if (ctl != 0) break;
-    const float al = sh_ab[0], bt = sh_ab[1];
+    const float al = static_cast<float>(sh_ab[0]), bt = static_cast<float>(sh_ab[1]);
     int k = 0, kg = 0, u0 = u;
     for (; u < nwu; u += tm.G, ++k) {
       if (k > 0 && wk >= 0) {
         y = gather(u, k, wcur, 1, &m, &lead);
         if (lead) own_load();
       }
-      float2 part = make_float2(0.0f, 0.0f);
+      double2 part = make_double2(0.0, 0.0);
       if (wk >= 0 && lead) {
         if (it == 0) {
           zv = y;
@@ -860,8 +859,8 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
         stcg(vx + m, xv);
         stcg(vr + m, r);
         stcg(wnext + m, wv);
-        const float tr = r * rs, tw = wv * rs;
-        part = make_float2(tr * tr, tw * tr);
+        const double tr = r * rs, tw = wv * rs;
+        part = make_double2(tr * tr, tw * tr);
       }
       warp_part2(kg, part);
       if (++kg == kUnitGroup && u + tm.G < nwu) {
@@ -879,7 +878,7 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
   __syncthreads();
   *status_out = ctl >= 16 ? ctl - 16 : FCT_OK;
   *iters_out = sh_ctl[1];
-  *gamma_out = static_cast<double>(sh_ab[2]) * gamma0;
+  *gamma_out = sh_ab[2] * gamma0;
   __syncthreads();
   return true;
 }
@@ -948,7 +947,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
     if (!team_sync(tm)) return false;
   }
   const double gamma0 = team_sum<BT>(P.part_c, ncc, red);
-  if (J.flags & kJobPrepareOnly) return true;  // b and s = A^T b are in place for the cluster solver
+  if (J.flags & kJobPrepareOnly) return true;  // the DCT stage alone: b and s = A^T b are in place
 
   int status = FCT_OK, iters = 0, refines = 0;
   double gfinal = gamma0;
@@ -1087,6 +1086,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
         for (;;) {
           if (ld_acquire_sys_i32(&a.ring->stop) != 0) break;
           if (ld_volatile_i32(&a.ls->exiting) != 0) break;  // the launch is winding down
+          if (ld_volatile_i32(&a.ls->err) != 0) break;      // a wait expired somewhere: stop claiming
           const unsigned long long tail = ld_acquire_sys_u64(&a.ring->tail);
           const unsigned int h = ld_volatile_i32(reinterpret_cast<const int*>(&a.ls->queue_head));
           if (h < tail) {
@@ -1121,7 +1121,30 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
       const SolveJob J = s_jobdesc;
       __syncthreads();
       if (j < 0) break;
-      if (!solve_job<BT, SV>(J, tm, red, dsm, a.smem_bytes)) return;
+      if (!solve_job<BT, SV>(J, tm, red, dsm, a.smem_bytes)) {
+        // Abandoned (a bounded wait expired in this team or another one): the
+        // job is reported finished with the launch's error code, the error is
+        // published in the ring for the host, the job no longer counts as
+        // busy, and the launch winds down (the host does not relaunch it).
+        if (tm.rank == 0 && threadIdx.x == 0) {
+          const int err = ld_volatile_i32(&a.ls->err);
+          fct_report rep;
+          rep.status = err != 0 ? err : static_cast<int>(FCT_ERR_TIMEOUT);
+          rep.iterations = 0;
+          rep.refinements = 0;
+          rep.reserved = 0;
+          rep.rel_normal_residual = 0.0;
+          rep.gamma0 = 0.0;
+          *J.report = rep;
+          st_release_sys_i32(&a.ring->err, rep.status);
+          __threadfence_system();
+          st_release_sys_i32(&a.ring->slots[j % kRingSize].done, 1);
+          atomicExch(&a.ls->exiting, 1);
+          __threadfence();
+          atomicSub(&a.ls->busy, 1);
+        }
+        return;
+      }
       if (tm.rank == 0 && threadIdx.x == 0) {
         __threadfence_system();
         st_release_sys_i32(&a.ring->slots[j % kRingSize].done, 1);

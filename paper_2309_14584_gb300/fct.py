@@ -52,7 +52,6 @@ class fct_options(ctypes.Structure):
         ("normal_matrix", ctypes.c_int),
         ("grid_kind", ctypes.c_int),
         ("entries_per_lane", ctypes.c_int),
-        ("cluster_solve", ctypes.c_int),
         ("plan_build", ctypes.c_int),
     ]
 
@@ -85,7 +84,6 @@ class fct_plan_info(ctypes.Structure):
         ("coef_lanes", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
         ("normal_nnz", ctypes.c_int64),
-        ("cluster_blocks", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -102,6 +102,8 @@ class ServingEngine:
                 t = F.fct_server_submit(self.server, self.slots[s][k], inputs[requests[i][2]], outputs[i])
                 in_flight[t] = (i, s, k, time.perf_counter() - t0)
             for t in list(in_flight):
+                # a device-side error of the serving launch (a bounded wait that
+                # expired) comes back as an exception here and ends the run
                 rep = F.fct_server_poll(self.server, t)
                 if rep is not None:
                     i, s, k, t_sub = in_flight.pop(t)

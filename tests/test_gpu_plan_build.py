@@ -58,7 +58,7 @@ def test_device_tables_equal_host_tables(name, mk, opts):
             assert np.array_equal(th[k], td[k]), k
         for k in ("wcsr", "wcm"):
             assert np.array_equal(_bits(th[k]), _bits(td[k])), k
-        for k in ("R", "M", "grid_blocks", "coef_lanes", "device_bytes", "normal_nnz", "cluster_blocks"):
+        for k in ("R", "M", "grid_blocks", "coef_lanes", "device_bytes", "normal_nnz"):
             assert ph.info[k] == pd.info[k], k
     finally:
         ph.close()

@@ -118,3 +118,76 @@ def test_run_times_out_when_nothing_finishes(monkeypatch):
     eng, srv = _engine(monkeypatch, shapes, budget=1e9, max_slots=1, work_polls=10**9)
     with pytest.raises(TimeoutError):
         eng.run([(0.0, 0, "in")], {"in": "x"}, ["o"], timeout_s=0.2)
+
+
+class _FailingServer(_FakeServer):
+    """The launch abandons its jobs after the `fail_after`-th poll: the job in
+    progress is reported finished with FCT_ERR_TIMEOUT, and every later poll
+    of an unfinished job raises the launch's error (as fct_server_poll does
+    once the device has published an error in the ring)."""
+
+    def __init__(self, work_polls, fail_after):
+        super().__init__(work_polls)
+        self.polls = 0
+        self.fail_after = fail_after
+        self.failed = False
+
+    def poll(self, t):
+        self.polls += 1
+        if self.polls >= self.fail_after and not self.failed:
+            self.failed = True
+            self.jobs[t][0] = 0
+            if self.jobs[t][1] in self.in_flight_handles:
+                self.in_flight_handles.remove(self.jobs[t][1])
+            return {"status": 4, "iterations": 0, "refinements": 0, "rel_normal_residual": 0.0, "gamma0": 0.0}
+        if self.failed and self.jobs[t][0] > 0:
+            raise RuntimeError("FCT_ERR_TIMEOUT: the serving launch abandoned its jobs after a device-side error")
+        return super().poll(t)
+
+
+def test_device_error_ends_the_run_promptly(monkeypatch):
+    shapes = [_shape(50)]
+    srv = _FailingServer(work_polls=4, fail_after=3)
+    fake = types.SimpleNamespace(
+        Plan=_FakePlan,
+        fct_server_create=lambda *a: srv,
+        fct_server_submit=lambda s, plan, x, c: s.submit(plan, x, c),
+        fct_server_poll=lambda s, t: s.poll(t),
+        fct_server_destroy=lambda s: None,
+    )
+    monkeypatch.setattr(serving, "F", fake)
+    eng = serving.ServingEngine(shapes, hbm_budget_bytes=1e9, max_slots_per_shape=3)
+    import time
+    t0 = time.perf_counter()
+    with pytest.raises(RuntimeError, match="device-side error"):
+        eng.run([(0.0, 0, "in") for _ in range(6)], {"in": "x"}, [f"o{i}" for i in range(6)], timeout_s=30)
+    assert time.perf_counter() - t0 < 5.0   # the error ends the run, not the run's own time limit
+
+
+def test_failed_job_report_reaches_the_summary(monkeypatch):
+    """A job the device reports finished with an error status is counted as
+    not converged by the latency summary."""
+    shapes = [_shape(50)]
+    srv = _FailingServer(work_polls=2, fail_after=10**9)
+    orig = srv.poll
+
+    def poll(t):
+        rep = orig(t)
+        if rep is not None and t == 1:
+            rep = dict(rep, status=4)
+        return rep
+
+    srv.poll = poll
+    fake = types.SimpleNamespace(
+        Plan=_FakePlan,
+        fct_server_create=lambda *a: srv,
+        fct_server_submit=lambda s, plan, x, c: s.submit(plan, x, c),
+        fct_server_poll=lambda s, t: s.poll(t),
+        fct_server_destroy=lambda s: None,
+    )
+    monkeypatch.setattr(serving, "F", fake)
+    eng = serving.ServingEngine(shapes, hbm_budget_bytes=1e9, max_slots_per_shape=2)
+    res = eng.run([(0.0, 0, "in") for _ in range(3)], {"in": "x"}, ["a", "b", "c"], timeout_s=30)
+    summ = serving.latency_summary(res, [50] * 3)
+    assert not summ["all_converged"]
+    assert sorted(r["report"]["status"] for r in res) == [0, 0, 4]

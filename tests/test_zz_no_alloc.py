@@ -48,6 +48,28 @@ def test_noalloc_matches_execute_on_consecutive_calls(mk, prec):
     plan.close()
 
 
+def test_noalloc_calls_take_no_device_memory():
+    """After one warm call (which may load kernels), further calls leave the
+    device's free memory unchanged: the workspace is the fixed array, and the
+    samples, outputs and plan exist beforehand."""
+    w = W.config_d6_gausscos()
+    plan = F.Plan(w.support, w.sizes, w.nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
+    samples = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    plan.sample(w.family, w.params, samples)
+    out = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    F.fct_execute_noalloc(plan.handle, samples, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rep = F.fct_execute_noalloc(plan.handle, samples, out)
+        assert rep["status"] == 0
+        F.fct_execute_noalloc(plan.handle, samples, out, report=False)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    plan.close()
+
+
 def test_noalloc_refuses_plans_beyond_its_array():
     """A 200 x 200 x 130 grid (5.2 million samples) needs more than 32 MiB of workspace."""
     support = np.zeros((8, 3), dtype=np.uint16)
