@@ -383,6 +383,24 @@ fct_status fct_evaluate(fct_plan plan, const double* coeffs, int64_t npoints, co
  */
 fct_status fct_measure_team_barrier(int blocks, int block_threads, int rounds, double* us_per_barrier);
 
+/*
+ * Measurement utilities (no counterpart in the paper): the on-chip roofs of a
+ * solver whose working set stays in L2, measured on the current device.  Each
+ * allocates and frees its own buffer, synchronises the device and changes no
+ * device setting.
+ *   fct_measure_l2: a buffer of `bytes` (1 to 96 MiB, so that it fits in L2)
+ *     is read once to make it resident, then `passes` more times with 16-byte
+ *     loads that bypass L1: *read_gbs = bytes read / time.  Then 8-byte loads
+ *     at pseudo-random positions of the same buffer (the pattern of the alias
+ *     gathers): *gather_gloads = 1e9 loads/s, *gather_sector_gbs = 32-byte
+ *     sectors moved per second in GB/s (either may be NULL).
+ *   fct_measure_fp64: independent FP64 fma chains in registers, `iters` fmas
+ *     per chain: *tflops = 2 flops per fma / time.
+ */
+fct_status fct_measure_l2(int64_t bytes, int passes, double* read_gbs, double* gather_gloads,
+                          double* gather_sector_gbs);
+fct_status fct_measure_fp64(int iters, double* tflops);
+
 /* Release a plan's device memory (synchronises the device first). NULL is OK. */
 fct_status fct_destroy(fct_plan plan);
 

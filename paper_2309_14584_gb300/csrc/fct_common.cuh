@@ -122,8 +122,55 @@ __device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_doub
 __device__ __forceinline__ double pzero(double) { return 0.0; }
 __device__ __forceinline__ double2 pzero(double2) { return make_double2(0.0, 0.0); }
 
-template <int NW, typename PT>
-__device__ bool phase_end(Team& tm, const PT (*wpart)[NW], PT* part, int u0, int nk) {
+// ---------------------------------------------------------------------------
+// Sums of squares of FP32 vectors at FP64 accuracy on the FP32 pipe
+// (double-float arithmetic): the square of a float is exact as a pair
+// hi + lo (hi = v v rounded, lo = fma(v, v, -hi)), and pairs are added with
+// Knuth's two-sum, so a warp's sum carries about 48 significant bits.  GB300
+// runs FP64 at a small fraction of its FP32 rate, so the FP32 inner solves
+// form their inner products this way and convert each warp's pair to FP64
+// once per group of units (widen); sums across warps and units are FP64.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+  const float2 s = df_two_sum(x.x, y.x);
+  const float e = s.y + (x.y + y.y);
+  const float hi = s.x + e;
+  return make_float2(hi, e - (hi - s.x));
+}
+__device__ __forceinline__ float2 df_square(float t) {
+  const float hi = t * t;
+  return make_float2(hi, fmaf(t, t, -hi));
+}
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+  return v;
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double2 widen(double2 v) { return v; }
+__device__ __forceinline__ double widen(float2 v) { return static_cast<double>(v.x) + static_cast<double>(v.y); }
+
+// Per-warp partial of a sum of squares: FP64 for FP64 vectors, a double-float
+// pair for FP32 vectors.
+template <typename V> struct SqPart;
+template <> struct SqPart<double> { using T = double; };
+template <> struct SqPart<float> { using T = float2; };
+__device__ __forceinline__ double sq_part(double v, double scale) {
+  const double t = v * scale;
+  return t * t;
+}
+__device__ __forceinline__ float2 sq_part(float v, double scale) { return df_square(v * static_cast<float>(scale)); }
+__device__ __forceinline__ double pzero_part(double) { return 0.0; }
+__device__ __forceinline__ float2 pzero_part(float2) { return make_float2(0.0f, 0.0f); }
+
+template <int NW, typename WT, typename PT>
+__device__ bool phase_end(Team& tm, const WT (*wpart)[NW], PT* part, int u0, int nk) {
   __shared__ int s_ok2;
   __syncthreads();
   tm.epoch += 1;
@@ -131,7 +178,7 @@ __device__ bool phase_end(Team& tm, const PT (*wpart)[NW], PT* part, int u0, int
     if (static_cast<int>(threadIdx.x) < nk) {
       PT v = pzero(PT{});
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v = padd(v, wpart[threadIdx.x][w]);
+      for (int w = 0; w < NW; ++w) v = padd(v, widen(wpart[threadIdx.x][w]));
       stcg(part + u0 + static_cast<int>(threadIdx.x) * tm.G, v);
     }
     __syncwarp();

@@ -432,11 +432,14 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
 // unit's partial is the fixed-order sum of its warps' sums, so partials (and
 // the result) do not depend on the team size.
 //
-// The inner products that give alpha and beta (|q|^2, |s|^2) are always
-// formed and reduced in FP64, also when the vectors are FP32 (V = float, the
-// inner solve of the mixed path): each owner squares its value in FP64, and
-// the per-unit partials are summed in a fixed order.  alpha, beta and the
-// stopping test are computed once per block by one thread and broadcast.
+// The inner products that give alpha and beta (|q|^2, |s|^2) are formed at
+// FP64 accuracy in a fixed order: FP64 squares and sums for FP64 vectors;
+// for FP32 vectors (V = float, the inner solve of the mixed path) exact
+// squares summed in double-float arithmetic inside a warp (SqPart), then FP64
+// across warps and units.  Squares are taken after scaling by a power of two
+// near 1/sqrt(gamma0) (exact), which keeps the FP32 squares of late
+// iterations in range.  alpha, beta and the stopping test are computed once
+// per block by one thread and broadcast.
 // On entry sp[m].x = right-hand side, x = 0, gamma0 = |s|^2 (> 0).  Stops when
 // gamma <= tol^2 gamma0, after max_iter (FCT_ERR_NOCONV) or, if stall > 0,
 // when gamma has not decreased for `stall` iterations.  All threads of all
@@ -450,8 +453,9 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
                           typename Vec2<V>::T* sp, V* q, XT* x, double gamma0, double tol, int max_iter, int stall,
                           int* iters_out, double* gamma_out, int* status_out, double* red) {
   using V2 = typename Vec2<V>::T;
+  using PT = typename SqPart<V>::T;
   constexpr int NW = BT / 32 - 1;  // worker warps
-  __shared__ double wpart[kUnitGroup][NW];
+  __shared__ PT wpart[kUnitGroup][NW];
   __shared__ double sh_ab[2];      // beta, alpha
   __shared__ int sh_ctl[3];        // stop flag, status, iterations
   *status_out = FCT_OK;
@@ -465,17 +469,16 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   const int wk = static_cast<int>(threadIdx.x) - 32;  // worker index; warp 0 has wk < 0
   const int warp = static_cast<int>(threadIdx.x >> 5) - 1;
   const int lane32 = threadIdx.x & 31;
-  const double rs = 1.0 / sqrt(gamma0);   // squares are taken relative to gamma0
-  const double tol2 = tol * tol;
-  // thread 0's state (relative gamma)
-  double gam = 1.0, best = 1.0;
+  int e0 = 0;
+  frexp(gamma0, &e0);
+  const double rs = ldexp(1.0, -(e0 / 2));  // power of two near 1/sqrt(gamma0): exact scaling
+  const double c0 = gamma0 * rs * rs;       // gamma0 in scaled units (in [1/4, 4))
+  const double tol2 = tol * tol * c0;
+  // thread 0's state (scaled gamma)
+  double gam = c0, best = c0;
   int it = 0, best_it = 0;
   bool first = true;
-  auto relsq = [&](V v) {
-    const double t = static_cast<double>(v) * rs;
-    return t * t;
-  };
-  auto warp_part = [&](int kk, double v) {
+  auto warp_part = [&](int kk, PT v) {
     v = warp_sum(v);
     if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
   };
@@ -484,7 +487,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     if (threadIdx.x < nk) {
       double v = 0.0;
 #pragma unroll
-      for (int w2 = 0; w2 < NW; ++w2) v += wpart[threadIdx.x][w2];
+      for (int w2 = 0; w2 < NW; ++w2) v += widen(wpart[threadIdx.x][w2]);
       stcg(part + u0 + threadIdx.x * tm.G, v);
     }
     __syncthreads();
@@ -539,11 +542,11 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       for (; u < nru; u += tm.G, ++k) {
         if (k > 0 && wk >= 0) gather_a(u, k, &as, &ap, &row, &lead);
         if (u < nwide) wide_row_combine<NW>(wk, &as, &ap, &lead);
-        double part = 0.0;
+        PT part = pzero_part(PT{});
         if (wk >= 0 && lead) {
           const V qv = first ? as : fma(beta, ap, as);
           stcg(q + row, qv);
-          part = relsq(qv);
+          part = sq_part(qv, rs);
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && u + tm.G < nru) {
@@ -600,7 +603,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           own_load(c, &o, &xo);
           t = coef_gather<V, WT, SV>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
-        double part = 0.0;
+        PT part = pzero_part(PT{});
         if (wk >= 0 && lead) {
           const V pn = first ? o.x : fma(beta, o.y, o.x);
           const V sn = fma(-alpha, t, o.x);
@@ -609,7 +612,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           nv.y = pn;
           stcg(sp + m, nv);
           stcg(x + m, static_cast<XT>(fma(static_cast<XT>(alpha), static_cast<XT>(pn), xo)));
-          part = relsq(sn);
+          part = sq_part(sn, rs);
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && c + tm.G < ncc) {
@@ -631,7 +634,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   __syncthreads();
   *status_out = sh_ctl[1];
   *iters_out = sh_ctl[2];
-  *gamma_out = sh_ab[0] * gamma0;
+  *gamma_out = sh_ab[0] / (rs * rs);
   __syncthreads();
   return true;
 }

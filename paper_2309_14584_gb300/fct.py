@@ -133,6 +133,9 @@ SIGNATURES = [
     ("fct_server_destroy", ctypes.c_int, [_P]),
     ("fct_selftest_wait_timeout", ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(ctypes.c_double)]),
+    ("fct_measure_l2", ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    ("fct_measure_fp64", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     ("fct_alias_tables_host", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, ctypes.c_int, _P, _P, ctypes.c_int, _P,
                                              _P, _P, ctypes.POINTER(ctypes.c_int64)]),
 ]
@@ -332,6 +335,20 @@ def fct_measure_team_barrier(blocks: int, block_threads: int = 256, rounds: int 
     us = ctypes.c_double()
     _check(lib().fct_measure_team_barrier(blocks, block_threads, rounds, ctypes.byref(us)))
     return us.value
+
+
+def fct_measure_l2(bytes_: int = 32 << 20, passes: int = 200) -> dict:
+    """L2 read bandwidth (GB/s) and random 8-byte gather rate of the current device."""
+    r, g, s = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().fct_measure_l2(bytes_, passes, ctypes.byref(r), ctypes.byref(g), ctypes.byref(s)))
+    return {"read_gbs": r.value, "gather_gloads_per_s": g.value, "gather_sector_gbs": s.value}
+
+
+def fct_measure_fp64(iters: int = 1 << 16) -> float:
+    """FP64 fma rate of the current device in TFLOP/s."""
+    t = ctypes.c_double()
+    _check(lib().fct_measure_fp64(iters, ctypes.byref(t)))
+    return t.value
 
 
 def fct_plan_apply(plan: int, x, y, transpose: bool = False, stream=None) -> np.ndarray:
