@@ -116,6 +116,14 @@ typedef struct {
                          FCT_PLAN_BUILD_HOST (1) in host C++.  Both give the same
                          tables bit for bit (fct_plan_tables).  The device build
                          needs transient scratch of about 110 bytes per entry (K N). */
+  int tensor_dct;     /* DCT passes on the tensor cores (Algorithm 3's per-grid DCT as
+                         BF16 digit-slice products with exact FP32 accumulation,
+                         FP64-accurate): 0 = auto (grids whose longest axis has
+                         64 to 1024 points), 1 = every grid with an active axis of at
+                         most 1024 points, -1 = off (FP64 units only).  Used by
+                         fct_execute, fct_execute_host and fct_plan_rhs; batches,
+                         serving and fct_execute_noalloc transform every grid on
+                         the FP64 units.                                              */
 } fct_options;
 
 #define FCT_PLAN_BUILD_AUTO 0
@@ -143,6 +151,7 @@ typedef struct {
   int32_t coef_lanes;
   int64_t device_bytes;     /* tables + workspace held on the device               */
   int64_t normal_nnz;       /* nonzeros of W = A^T A when the plan stores it, else 0 */
+  int64_t tensor_dct_grids; /* grids whose DCT runs on the tensor cores (fct_execute) */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,

@@ -286,6 +286,11 @@ struct fct_plan_s {
   bool stage_values = false;                // single launches stage the CG loop's entry values too
   double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
+  // DCT passes on the tensor cores (grids with a long axis; null when none):
+  // host description and device tables shared with clones, own workspace
+  std::shared_ptr<TcHost> tc;
+  std::shared_ptr<TcDevice> tc_dev;
+  std::shared_ptr<TcWork> tc_work;
 };
 
 namespace {
@@ -436,6 +441,19 @@ SolveJob make_job(fct_plan P, const double* samples, double* coeffs, fct_report*
   return j;
 }
 
+unsigned long long timeout_ns(fct_plan P);
+
+// Single-transform executes of plans with tensor-core grids: their DCT passes
+// run first (same stream), and the job skips them (kJobTcDct).
+fct_status run_tc_passes(fct_plan P, const double* samples, cudaStream_t st, SolveJob* job) {
+  if (!P->tc) return FCT_OK;
+  const fct_status s = tc_run(*P->tc, *P->tc_dev, *P->tc_work, samples, P->hp.y0, P->hp.y1, &P->ls->err,
+                              timeout_ns(P), st);
+  if (s != FCT_OK) return s;
+  job->flags |= kJobTcDct;
+  return FCT_OK;
+}
+
 unsigned long long timeout_ns(fct_plan P) {
   double t = P->opt.timeout_s > 0 ? P->opt.timeout_s : 4.0;
   return static_cast<unsigned long long>(t * 1e9);
@@ -521,6 +539,21 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     lane_class_counts(H, classes);
     epl = pick_entries_per_lane(classes, workers, wave, o.entries_per_lane);
     device_row_order(&H, epl);
+  }
+  // tensor-core DCT passes: which grids, their A slices and pass lists (may
+  // add the identity matrix to the DCT matrices, so before their upload)
+  if (o.tensor_dct < -1 || o.tensor_dct > 1) {
+    delete P;
+    return fail(FCT_ERR_INVALID_ARG, "tensor_dct must be -1, 0 or 1");
+  }
+  {
+    auto T = std::make_shared<TcHost>();
+    s = build_tc_host(&H, sizes, o.grid_kind, o.tensor_dct, T.get());
+    if (s != FCT_OK) {
+      delete P;
+      return fail(s, "tensor-core DCT set-up: a pass is too large");
+    }
+    if (!T->empty()) P->tc = T;
   }
   P->R = H.R;
   DevPlan& hp = P->hp;
@@ -744,7 +777,27 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   chk(up(P->d_ichunks, H.idct_chunks.data(), sizeof(DctChunk) * H.idct_chunks.size()));
   chk(up(P->d_emats, H.eval_mats.data(), sizeof(double) * H.eval_mats.size()));
   s = FCT_OK;
-  if (ue == cudaSuccess) s = choose_shape(P);
+  if (ue == cudaSuccess && P->tc) {
+    std::vector<int32_t> rb, rk;
+    final_pass_rows_for(H, P->tc->gfinal, &rb, &rk);
+    auto dev = std::make_shared<TcDevice>();
+    auto wk = std::make_shared<TcWork>();
+    s = tc_upload(*P->tc, rb, rk, dev.get());
+    if (s == FCT_OK) s = tc_alloc_work(*P->tc, wk.get());
+    if (s == FCT_OK) {
+      P->tc_dev = dev;
+      P->tc_work = wk;
+      hp.npass_tc = P->tc->npass_fp64;
+      hp.pass_chunk_off_tc = dev->pass_chunk_off;
+      hp.dct_chunks_tc = dev->dct_chunks;
+      hp.gfinal_tc = dev->gfinal;
+      hp.rowbase_tc = dev->rowbase;
+      hp.rowk_tc = dev->rowk;
+      P->tc->a_bits.clear();
+      P->tc->a_bits.shrink_to_fit();
+    }
+  }
+  if (ue == cudaSuccess && s == FCT_OK) s = choose_shape(P);
   if (ue == cudaSuccess && s == FCT_OK) chk(up(P->dp, &hp, sizeof(DevPlan)));
   if (ue == cudaSuccess && s == FCT_OK && nnodes > 0) {
     cheb_table_kernel<<<static_cast<unsigned>((nnodes + 127) / 128), 128>>>(P->d_node_pos, static_cast<int>(nnodes),
@@ -800,6 +853,9 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->coef_lanes = P->hp.coef_lanes;
   info->device_bytes = static_cast<int64_t>(P->dbytes);
   info->normal_nnz = P->hp.n_w_units > 0 ? static_cast<int64_t>(P->w_rowptr_h.back()) : 0;
+  info->tensor_dct_grids = 0;
+  if (P->tc)
+    for (char g : P->tc->grid_tc) info->tensor_dct_grids += g ? 1 : 0;
   return FCT_OK;
 }
 
@@ -927,7 +983,9 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
   a.ls = P->ls;
   a.timeout_ns = timeout_ns(P);
   a.smem_bytes = P->smem_bytes;
-  fct_status s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
+  fct_status s = run_tc_passes(P, samples, st, &a.single);
+  if (s != FCT_OK) return s;
+  s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
   if (s != FCT_OK) return s;
   if (rep) return read_report(P, P->drep, st, rep);
   return FCT_OK;
@@ -963,7 +1021,9 @@ fct_status fct_plan_rhs(fct_plan P, const double* samples, double* b, int64_t* b
   a.ls = P->ls;
   a.timeout_ns = timeout_ns(P);
   a.smem_bytes = P->smem_bytes;
-  fct_status s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
+  fct_status s = run_tc_passes(P, samples, st, &a.single);
+  if (s != FCT_OK) return s;
+  s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
   if (s != FCT_OK) return s;
   FCT_CUDA(cudaMemcpyAsync(b, P->hp.b, sizeof(double) * P->R, cudaMemcpyDeviceToDevice, st));
   FCT_CUDA(cudaStreamSynchronize(st));
@@ -1111,6 +1171,17 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
   C->ru_first = src->ru_first;
   C->rowptr_h = src->rowptr_h;
   C->w_rowptr_h = src->w_rowptr_h;
+  C->tc = src->tc;
+  C->tc_dev = src->tc_dev;
+  if (C->tc) {
+    auto wk = std::make_shared<TcWork>();
+    const fct_status ts = tc_alloc_work(*C->tc, wk.get());
+    if (ts != FCT_OK) {
+      delete C;
+      return ts;
+    }
+    C->tc_work = wk;
+  }
   // its own workspace, DevPlan copy, launch state and report
   DevPlan& hp = C->hp;
   const size_t M = static_cast<size_t>(std::max<int64_t>(C->M, 1)), R = static_cast<size_t>(C->R),

@@ -45,6 +45,71 @@ struct GridFinal {
   int32_t in_sel;          // 0 = caller samples, 1 = y0, 2 = y1
 };
 
+// ---------------------------------------------------------------------------
+// DCT passes on the tensor cores (grids with a long axis).  An axis pass over a
+// grid tensor of shape (pre, n, post) is the product Y = C X of the n x n DCT
+// matrix with the n x (pre post) matrix of the tensor's fibres.  Both factors
+// are split into kTcSlices slices of 8-bit signed digits (base 128, balanced)
+// below a per-row (C) and per-column (X) power of two, so every slice is
+// exact in BF16; the products of slice pairs with digit sum g (36 products)
+// accumulate exactly in FP32 on the tensor cores (|sum| < 2^24 for n <= 1024)
+// and the kTcSlices sums are combined in integers, then converted to FP64 once
+// per output: results agree with an FP64 product to about 1e-16 relative to
+// sum |C||X|.  M tile 128 rows of C, N tile 64 fibres, K step 16.
+// ---------------------------------------------------------------------------
+constexpr int kTcSlices = 8;
+constexpr int kTcM = 128, kTcN = 64, kTcK = 16;
+constexpr int kTcATile = kTcM * kTcK * 2;             // bytes of one A slice of one K step
+constexpr int kTcBTile = kTcN * kTcK * 2;             // bytes of one B slice of one K step
+constexpr int kTcAStep = kTcSlices * kTcATile;        // 32 KB: all A slices of one K step
+constexpr int kTcBStep = kTcSlices * kTcBTile;        // 16 KB
+constexpr int kTcStageBytes = kTcAStep + kTcBStep;    // one pipeline stage in shared memory
+constexpr int kTcStages = 4;
+constexpr int kTcMinAxis = 64;                        // auto: grids whose longest axis has >= 64 points
+constexpr int kTcMaxAxis = 1024;                      // exact FP32 accumulation holds up to here
+constexpr int kTcNonFinite = -100000;                 // column exponent of a fibre holding NaN / Inf
+
+// One tensor-core pass over one grid.
+struct TcGridPass {
+  int64_t base;      // the grid's first element in samples / y0 / y1
+  int64_t a_off;     // byte offset of the A slices of this axis length
+  int64_t b_off;     // byte offset of this pass's B slices in the B workspace
+  int32_t n, post;   // axis length and stride: the tensor is (pre, n, post)
+  int32_t ncols;     // pre * post fibres
+  int32_t ksteps;    // ceil(n / 16)
+  int32_t mtiles, ntiles;
+  int32_t e_off;     // first row exponent of this axis length
+  int32_t f_off;     // first column exponent of this pass in the exponent workspace
+  int8_t in_sel, out_sel;  // 0 = caller samples, 1 = y0, 2 = y1
+  int16_t pad0;
+  int32_t pad1;
+};
+static_assert(sizeof(TcGridPass) == 64, "TcGridPass layout");
+
+// Host description of a plan's tensor-core DCT (empty when no grid uses it).
+struct TcHost {
+  std::vector<char> grid_tc;              // [K] 1 = the grid's DCT runs on the tensor cores
+  int npass = 0;                          // tensor-core passes (most active axes of a tensor-core grid)
+  std::vector<TcGridPass> gp;             // all passes, pass-major
+  std::vector<int32_t> gp_off;            // [npass + 1]
+  std::vector<int32_t> split_tasks;       // pairs {gp, ntile}
+  std::vector<int32_t> split_off;         // [npass + 1] in pairs
+  std::vector<int32_t> gemm_tasks;        // quads {gp, mtile, ntile, 0}
+  std::vector<int32_t> gemm_off;          // [npass + 1] in quads
+  std::vector<uint16_t> a_bits;           // BF16 bits of every A slice
+  std::vector<int32_t> a_exp;             // row exponents
+  int64_t b_bytes = 0;                    // B workspace (largest pass)
+  int64_t f_count = 0;                    // column-exponent workspace (largest pass)
+  // the solver's DCT for plans run with the tensor-core passes: passes of the
+  // grids left to the FP64 units, and a last pass that reads the finished
+  // transform of every tensor-core grid (identity)
+  int npass_fp64 = 0;
+  std::vector<int32_t> pass_chunk_off;
+  std::vector<DctChunk> dct_chunks;
+  std::vector<GridFinal> gfinal;
+  bool empty() const { return npass == 0; }
+};
+
 // Everything the solver kernel needs about one plan; lives in device memory.
 struct DevPlan {
   int32_t N, R, K, D;
@@ -107,7 +172,14 @@ struct DevPlan {
   const double* s_init;      // [N] or nullptr
   double2* hist;             // [hist_cap] (alpha_k, beta_k) or nullptr
   int32_t hist_cap;
-  int32_t pad_hist;
+  int32_t npass_tc;          // jobs with kJobTcDct: FP64 passes left after the tensor-core passes
+  // DCT of jobs with kJobTcDct (the tensor-core grids are already transformed
+  // in y0 / y1): their pass lists, last passes and last-pass rows
+  const int32_t* pass_chunk_off_tc;
+  const DctChunk* dct_chunks_tc;
+  const GridFinal* gfinal_tc;
+  const int32_t* rowbase_tc;
+  const int32_t* rowk_tc;
 };
 
 // One transform of a launch.
@@ -119,11 +191,13 @@ struct SolveJob {
   int32_t precision;
   int32_t max_iter;
   int32_t max_refine;
-  int32_t flags;             // kJobPrepareOnly: stop after b and s = A^T b (the DCT stage alone)
+  int32_t flags;             // kJobPrepareOnly: stop after b and s = A^T b (the DCT stage alone);
+                             // kJobTcDct: the tensor-core grids' DCT is done (y0 / y1)
   double tol;
   double inner_tol;
 };
 constexpr int32_t kJobPrepareOnly = 1;
+constexpr int32_t kJobTcDct = 2;
 
 // Barrier of one team: a monotonic arrival counter (target = G x barrier
 // number) and an exit counter that lets the last block reset it.
@@ -276,6 +350,48 @@ void normal_matrix(const HostTables& H, std::vector<int32_t>* rowptr, std::vecto
 
 // Per-row inputs of the fused last DCT pass (after device_row_order).
 void final_pass_rows(const HostTables& H, std::vector<int32_t>* rowbase, std::vector<int32_t>* rowk);
+
+// The same for the last passes `gfinal` (one per grid), from each row's sample
+// index H.rowsrc (the row's grid is found from the sample offsets).
+void final_pass_rows_for(const HostTables& H, const std::vector<GridFinal>& gfinal, std::vector<int32_t>* rowbase,
+                         std::vector<int32_t>* rowk);
+
+// Tensor-core DCT set-up: mode 0 = auto (grids whose longest active axis has
+// at least kTcMinAxis points), 1 = every grid with an active axis, -1 = none;
+// grids with an axis longer than kTcMaxAxis stay on the FP64 units.  Fills
+// *T (empty when no grid qualifies); H must hold the DCT set-up of
+// build_host_tables.  Adds the identity matrix to H->dct_mats if needed.
+fct_status build_tc_host(HostTables* H, const int32_t* sizes, int grid_kind, int mode, TcHost* T);
+
+// Device copy of a TcHost (read-only part) and one workspace.
+struct TcDevice {
+  void* mem = nullptr;
+  const TcGridPass* gp = nullptr;
+  const int32_t* split_tasks = nullptr;
+  const int32_t* gemm_tasks = nullptr;
+  const unsigned char* a = nullptr;
+  const int32_t* a_exp = nullptr;
+  int32_t* pass_chunk_off = nullptr;
+  DctChunk* dct_chunks = nullptr;
+  GridFinal* gfinal = nullptr;
+  int32_t* rowbase = nullptr;
+  int32_t* rowk = nullptr;
+  ~TcDevice();
+};
+struct TcWork {
+  void* mem = nullptr;
+  unsigned char* b = nullptr;
+  int32_t* f = nullptr;
+  ~TcWork();
+};
+fct_status tc_upload(const TcHost& T, const std::vector<int32_t>& rowbase, const std::vector<int32_t>& rowk,
+                     TcDevice* out);
+fct_status tc_alloc_work(const TcHost& T, TcWork* out);
+// Runs every tensor-core pass of the plan on `stream`: the finished transforms
+// of the tensor-core grids land in y0 / y1 as the solver's kJobTcDct jobs
+// expect.  A bounded wait that expires sets *err (the launch's error flag).
+fct_status tc_run(const TcHost& T, const TcDevice& D, const TcWork& Wk, const double* samples, double* y0,
+                  double* y1, int* err, unsigned long long timeout_ns, void* stream);
 
 // T_m(x) by the three-term recurrence.
 double cheb_T(int m, double x);

@@ -11,6 +11,7 @@
 // nonempty bins of grid l become rows row_off[l] .. row_off[l+1]-1 in
 // ascending bin order.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -522,6 +523,216 @@ void normal_matrix(const HostTables& H, std::vector<int32_t>* rowptr, std::vecto
     }
     (*rowptr)[m + 1] = static_cast<int32_t>(col->size());
   }
+}
+
+void final_pass_rows_for(const HostTables& H, const std::vector<GridFinal>& gfinal, std::vector<int32_t>* rowbase,
+                         std::vector<int32_t>* rowk) {
+  rowbase->resize(H.R);
+  rowk->resize(H.R);
+  for (int64_t r = 0; r < H.R; ++r) {
+    const int64_t src = H.rowsrc[r];
+    const int l = static_cast<int>(std::upper_bound(H.offsets.begin(), H.offsets.end(), src) - H.offsets.begin()) - 1;
+    const GridFinal& g = gfinal[l];
+    const int64_t bin = src - H.offsets[l];
+    const int64_t k = (bin / g.stride) % g.n;
+    (*rowbase)[r] = static_cast<int32_t>(H.offsets[l] + bin - k * g.stride);
+    (*rowk)[r] = static_cast<int32_t>(k);
+  }
+}
+
+namespace {
+
+// Balanced base-128 digits of round(v * 2^(56 - e)) (|v| < 2^e): the value is
+// sum_t digit[t] 2^(7 (7 - t)), digit[0] in [-128, 128], the others in
+// [-64, 63]; every digit is exact in BF16.
+void tc_digits(double v, int e, int32_t digit[kTcSlices]) {
+  int64_t x = std::llrint(std::ldexp(v, 56 - e));
+  for (int t = kTcSlices - 1; t >= 1; --t) {
+    const int64_t q = (x + 64) >> 7;  // floor((x + 64) / 128)
+    digit[t] = static_cast<int32_t>(x - q * 128);
+    x = q;
+  }
+  digit[0] = static_cast<int32_t>(x);
+}
+
+uint16_t bf16_bits_of_small_int(int32_t d) {
+  const float f = static_cast<float>(d);
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return static_cast<uint16_t>(u >> 16);  // exact: |d| <= 128 has at most 8 significant bits
+}
+
+// Byte offset of element (row r, k) inside one slice tile of `rows` x 16
+// (K-major, no swizzle: 8 x 16-byte core matrices, the two K halves 128
+// bytes apart, 8-row groups 256 bytes apart).
+inline int64_t tc_tile_offset(int r, int k) { return (r / 8) * 256 + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2; }
+
+}  // namespace
+
+fct_status build_tc_host(HostTables* Hp, const int32_t* sizes, int grid_kind, int mode, TcHost* T) {
+  HostTables& H = *Hp;
+  *T = TcHost{};
+  if (mode < 0) return FCT_OK;
+  const int K = H.K, D = H.D;
+  const bool first = grid_kind == FCT_GRID_FIRST_KIND;
+  std::vector<std::vector<int>> active(K);
+  std::vector<char> tc(K, 0);
+  bool any = false;
+  for (int l = 0; l < K; ++l) {
+    int longest = 0;
+    for (int i = 0; i < D; ++i)
+      if (sizes[l * D + i] >= 2) {
+        active[l].push_back(i);
+        longest = std::max(longest, sizes[l * D + i]);
+      }
+    if (!active[l].empty() && longest <= kTcMaxAxis && (mode == 1 || longest >= kTcMinAxis)) {
+      tc[l] = 1;
+      any = true;
+    }
+  }
+  if (!any) return FCT_OK;
+  T->grid_tc = tc;
+
+  // A slices of the DCT matrix of every axis length the tensor-core grids use
+  std::vector<int64_t> a_off_of(kTcMaxAxis + 1, -1);
+  std::vector<int32_t> e_off_of(kTcMaxAxis + 1, -1);
+  int64_t a_bytes = 0;
+  for (int l = 0; l < K; ++l) {
+    if (!tc[l]) continue;
+    for (int i : active[l]) {
+      const int n = sizes[l * D + i];
+      if (a_off_of[n] >= 0) continue;
+      const int ksteps = (n + kTcK - 1) / kTcK, mtiles = (n + kTcM - 1) / kTcM;
+      a_off_of[n] = a_bytes;
+      e_off_of[n] = static_cast<int32_t>(T->a_exp.size());
+      a_bytes += static_cast<int64_t>(mtiles) * ksteps * kTcAStep;
+      T->a_bits.resize(a_bytes / 2, 0);
+      T->a_exp.resize(T->a_exp.size() + static_cast<size_t>(mtiles) * kTcM, 0);
+      for (int k = 0; k < n; ++k) {
+        // row k of the pass matrix, as build_host_tables forms it
+        std::vector<double> row(n);
+        double m = 0.0;
+        for (int j = 0; j < n; ++j) {
+          double c;
+          if (first) {
+            const int64_t h = 2 * static_cast<int64_t>(n);
+            c = cos_pi_ratio((static_cast<int64_t>(k) * (2 * j + 1)) % (2 * h), h) / static_cast<double>(n);
+          } else {
+            const int64_t h = n - 1;
+            const double ek = (k == 0 || k == n - 1) ? 0.5 : 1.0;
+            const double ej = (j == 0 || j == n - 1) ? 0.5 : 1.0;
+            c = (2.0 * ek / static_cast<double>(h)) * ej * cos_pi_ratio((static_cast<int64_t>(j) * k) % (2 * h), h);
+          }
+          row[j] = c;
+          m = std::max(m, std::fabs(c));
+        }
+        int e = 0;
+        if (m > 0.0) std::frexp(m, &e);
+        T->a_exp[e_off_of[n] + k] = e;
+        const int mt = k / kTcM, r = k % kTcM;
+        for (int j = 0; j < n; ++j) {
+          int32_t dg[kTcSlices];
+          tc_digits(row[j], e, dg);
+          const int ks = j / kTcK, kk = j % kTcK;
+          for (int t = 0; t < kTcSlices; ++t) {
+            const int64_t byte = a_off_of[n] + ((static_cast<int64_t>(mt) * ksteps + ks) * kTcSlices + t) * kTcATile +
+                                 tc_tile_offset(r, kk);
+            T->a_bits[byte / 2] = bf16_bits_of_small_int(dg[t]);
+          }
+        }
+      }
+    }
+  }
+
+  // passes: pass p transforms the p-th active axis of every tensor-core grid
+  // (ping-pong y0 / y1 as the FP64 passes do)
+  int npass = 0;
+  for (int l = 0; l < K; ++l)
+    if (tc[l]) npass = std::max<int>(npass, static_cast<int>(active[l].size()));
+  T->npass = npass;
+  T->gp_off.assign(1, 0);
+  T->split_off.assign(1, 0);
+  T->gemm_off.assign(1, 0);
+  for (int p = 0; p < npass; ++p) {
+    int64_t b_off = 0, f_off = 0;
+    for (int l = 0; l < K; ++l) {
+      const int A = static_cast<int>(active[l].size());
+      if (!tc[l] || p >= A) continue;
+      const int axis = active[l][p];
+      TcGridPass g{};
+      g.base = H.offsets[l];
+      g.n = sizes[l * D + axis];
+      int64_t post = 1;
+      for (int i = axis + 1; i < D; ++i) post *= sizes[l * D + i];
+      const int64_t Tl = H.offsets[l + 1] - H.offsets[l];
+      g.post = static_cast<int32_t>(post);
+      g.ncols = static_cast<int32_t>(Tl / g.n);
+      g.ksteps = (g.n + kTcK - 1) / kTcK;
+      g.mtiles = (g.n + kTcM - 1) / kTcM;
+      g.ntiles = (g.ncols + kTcN - 1) / kTcN;
+      g.a_off = a_off_of[g.n];
+      g.e_off = e_off_of[g.n];
+      g.b_off = b_off;
+      g.f_off = static_cast<int32_t>(f_off);
+      g.in_sel = p == 0 ? 0 : static_cast<int8_t>(((p - 1) & 1) ? 2 : 1);
+      g.out_sel = static_cast<int8_t>((p & 1) ? 2 : 1);
+      b_off += static_cast<int64_t>(g.ntiles) * g.ksteps * kTcBStep;
+      f_off += static_cast<int64_t>(g.ntiles) * kTcN;
+      const int gi = static_cast<int>(T->gp.size());
+      T->gp.push_back(g);
+      for (int nt = 0; nt < g.ntiles; ++nt) {
+        T->split_tasks.push_back(gi);
+        T->split_tasks.push_back(nt);
+        for (int mt = 0; mt < g.mtiles; ++mt) {
+          T->gemm_tasks.push_back(gi);
+          T->gemm_tasks.push_back(mt);
+          T->gemm_tasks.push_back(nt);
+          T->gemm_tasks.push_back(0);
+        }
+      }
+    }
+    T->b_bytes = std::max(T->b_bytes, b_off);
+    T->f_count = std::max(T->f_count, f_off);
+    T->gp_off.push_back(static_cast<int32_t>(T->gp.size()));
+    T->split_off.push_back(static_cast<int32_t>(T->split_tasks.size() / 2));
+    T->gemm_off.push_back(static_cast<int32_t>(T->gemm_tasks.size() / 4));
+  }
+  if (T->f_count > (int64_t{1} << 31) || T->b_bytes > (int64_t{1} << 40)) return FCT_ERR_INVALID_ARG;
+
+  // the solver's DCT when the tensor-core passes ran first: the FP64 passes of
+  // the other grids (a pass list without the tensor-core grids' units), and an
+  // identity last pass that reads each tensor-core grid's finished transform
+  int32_t ident = -1;
+  for (const GridFinal& g : H.gfinal)
+    if (g.n == 1) ident = g.mat;
+  if (ident < 0) {
+    ident = static_cast<int32_t>(H.dct_mats.size());
+    H.dct_mats.push_back(1.0);
+  }
+  T->gfinal = H.gfinal;
+  for (int l = 0; l < K; ++l) {
+    if (!tc[l]) continue;
+    const int A = static_cast<int>(active[l].size());
+    GridFinal g{};
+    g.n = 1;
+    g.stride = 1;
+    g.mat = ident;
+    g.in_sel = ((A - 1) & 1) ? 2 : 1;
+    T->gfinal[l] = g;
+  }
+  T->pass_chunk_off.assign(1, 0);
+  for (int p = 0; p < H.npass; ++p) {
+    for (int32_t c = H.pass_chunk_off[p]; c < H.pass_chunk_off[p + 1]; ++c) {
+      const DctChunk& ch = H.dct_chunks[c];
+      const int l = static_cast<int>(std::upper_bound(H.offsets.begin(), H.offsets.end(), ch.base) -
+                                     H.offsets.begin()) - 1;
+      if (!tc[l]) T->dct_chunks.push_back(ch);
+    }
+    if (static_cast<int32_t>(T->dct_chunks.size()) == T->pass_chunk_off.back()) break;
+    T->pass_chunk_off.push_back(static_cast<int32_t>(T->dct_chunks.size()));
+    T->npass_fp64 = p + 1;
+  }
+  return FCT_OK;
 }
 
 }  // namespace fct

@@ -178,11 +178,13 @@ __device__ void dct_unit(const DevPlan& P, const double* mats, const double* __r
 }
 
 // Last pass at a nonempty bin: b[row] = sum_j C[k][j] in[rowbase + j*stride].
+// tcm: the tensor-core passes have transformed some grids completely; their
+// rows read the result (n = 1) through the kJobTcDct lists.
 __device__ __forceinline__ double dct_final_row(const DevPlan& P, const double* mats, const double* __restrict__ samples,
-                                                int row) {
-  const GridFinal g = P.gfinal[__ldg(P.rowgrid + row)];
-  const int k = __ldg(P.rowk + row);
-  const int base = __ldg(P.rowbase + row);
+                                                int row, bool tcm) {
+  const GridFinal g = (tcm ? P.gfinal_tc : P.gfinal)[__ldg(P.rowgrid + row)];
+  const int k = __ldg((tcm ? P.rowk_tc : P.rowk) + row);
+  const int base = __ldg((tcm ? P.rowbase_tc : P.rowbase) + row);
   const double* Ck = mats + g.mat + k * g.n;
   double acc = 0.0;
   if (g.in_sel == 0) {
@@ -916,17 +918,22 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
     }
     if (!team_sync(tm)) return false;
   } else {
-    // ---- full DCT-I axis passes
-    for (int pass = 0; pass < P.npass; ++pass) {
-      const int c0 = __ldg(P.pass_chunk_off + pass), c1 = __ldg(P.pass_chunk_off + pass + 1);
-      for (int c = c0 + tm.rank; c < c1; c += tm.G) dct_unit<BT>(P, T.mats, J.samples, P.dct_chunks[c]);
+    // ---- full DCT-I axis passes (kJobTcDct: only the grids left to the FP64
+    // units; the tensor-core passes ran before this launch)
+    const bool tcm = (J.flags & kJobTcDct) != 0;
+    const int npass = tcm ? P.npass_tc : P.npass;
+    const int32_t* pco = tcm ? P.pass_chunk_off_tc : P.pass_chunk_off;
+    const DctChunk* chunks = tcm ? P.dct_chunks_tc : P.dct_chunks;
+    for (int pass = 0; pass < npass; ++pass) {
+      const int c0 = __ldg(pco + pass), c1 = __ldg(pco + pass + 1);
+      for (int c = c0 + tm.rank; c < c1; c += tm.G) dct_unit<BT>(P, T.mats, J.samples, chunks[c]);
       if (!team_sync(tm)) return false;
     }
     // ---- last pass at the nonempty bins -> b ; x = 0
     for (int u = tm.rank; u < nre + nce; u += tm.G) {
       if (u < nre) {
         const int row = u * BT + threadIdx.x;
-        if (row < P.R) stcg(P.b + row, dct_final_row(P, T.mats, J.samples, row));
+        if (row < P.R) stcg(P.b + row, dct_final_row(P, T.mats, J.samples, row, tcm));
       } else {
         const int m = (u - nre) * BT + threadIdx.x;
         if (m < P.N) stcg(J.coeffs + m, 0.0);

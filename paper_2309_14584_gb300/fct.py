@@ -53,6 +53,7 @@ class fct_options(ctypes.Structure):
         ("grid_kind", ctypes.c_int),
         ("entries_per_lane", ctypes.c_int),
         ("plan_build", ctypes.c_int),
+        ("tensor_dct", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,7 @@ class fct_plan_info(ctypes.Structure):
         ("coef_lanes", ctypes.c_int32),
         ("device_bytes", ctypes.c_int64),
         ("normal_nnz", ctypes.c_int64),
+        ("tensor_dct_grids", ctypes.c_int64),
     ]
 
     def as_dict(self):
