@@ -59,6 +59,16 @@ PATH_OPTIONS = {   # precision: 0 = FCT_FP64, 1 = FCT_MIXED (include/fct.h)
 }
 
 
+# cases of --profile: (workload factory name, path options, plan options)
+PROFILE_CASES = {
+    "d10_mixed": ("config_d10_rational", "mixed", {}),
+    "d10_fp64": ("config_d10_rational", "fp64", {}),
+    "d6_mixed": ("config_d6_gausscos", "mixed", {}),
+    "d2_tensor_dct": ("tc_profile_workload", "mixed", {}),
+    "sparse_d100": ("sparse_profile_workload", "mixed", {}),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -81,6 +91,8 @@ def parse():
     ap.add_argument("--hetero-batch", type=int, default=HETERO_BATCH,
                     help="transforms of the heterogeneous batch leg (D 3..8, degree 6..14; 0 = skip)")
     ap.add_argument("--no-next-rows", action="store_true", help="skip the rows past the hot path")
+    ap.add_argument("--profile", default=None, choices=sorted(PROFILE_CASES),
+                    help="run only `--warmup` + `--steps` executes of one case, without timing (for ncu)")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -1001,10 +1013,62 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def tc_profile_workload():
+    """D=2, total degree 300 (N = 45451), 8 grids by Algorithm 1 with axes of
+    150 to 301 points (M = 322576 samples), Gaussian-cosine target: a plan
+    whose DCT runs on the tensor cores (the solve needs about 20 CG
+    iterations, so the DCT is a large share of the transform)."""
+    import workloads as W
+    sup = W.total_degree_support(2, 300)
+    sizes, nodes = W.l_grid(24, sup.shape[0], 2, 8, 150, 301)
+    return W.Workload("D2_d300_gausscos_K8", 2, 300, sup, sizes, nodes, W.FAMILY_GAUSSCOS, W.gausscos_params(24, 2),
+                      None, 1e-12, "mixed")
+
+
+def sparse_profile_workload():
+    """Sparse S^inf support at D = 100 (N = 2e4, 3 nonzero components per
+    index, degree <= 9), 1000 grids, seeded polynomial target."""
+    import workloads as W
+    D, d, N = 100, 9, 20_000
+    sup = W.sparse_infinity_support(13, D, d, N, 3)
+    sizes, nodes = W.l_grid(300, N, D, 10 * D, 1, d + 1)
+    c = W.poly_coefficients(10, sup)
+    return W.Workload("sparse_D100_N2e4_K1000", D, d, sup, sizes, nodes, W.FAMILY_POLY, c, c, 1e-12, "mixed")
+
+
+def run_profile(args):
+    """`--warmup` + `--steps` executes of one case, nothing timed or printed
+    but one status line: the command that ncu captures."""
+    import torch
+    import workloads as W
+    import paper_2309_14584_gb300 as F
+    from paper_2309_14584_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    wname, path, popts = PROFILE_CASES[args.profile]
+    w = getattr(W, wname)() if hasattr(W, wname) else globals()[wname]()
+    plan = F.Plan(w.support, w.sizes, w.nodes, **dict(PATH_OPTIONS[path], **popts))
+    x = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    fam = w.family | (F.fct.FCT_SAMPLE_FOLDED if w.family == W.FAMILY_POLY else 0)
+    plan.sample(fam, w.params, x)
+    c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    rep = None
+    for _ in range(args.warmup + args.steps):
+        rep = plan.execute(x, c)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": args.profile, "workload": w.name, "N": plan.N, "M": plan.M,
+                      "R": plan.info["R"], "K": plan.info["K"], "tensor_dct_grids": plan.info["tensor_dct_grids"],
+                      "report": rep}))
+    plan.close()
+
+
 def main():
     args = parse()
     if args.oracle_worker:
         oracle_worker(args.oracle_worker)
+        return
+    if args.profile:
+        run_profile(args)
         return
     if args.impl == "reference":
         run_reference(args)
