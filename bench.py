@@ -765,6 +765,28 @@ def run_next_rows(F, w, opts, flush, steps=20) -> dict:
                                     "peak_kind": "FP64 fma rate measured live by fct_measure_fp64"}}
     out["evaluate"]["roofline"]["frac"] = out["evaluate"]["roofline"]["achieved"] / out["evaluate"]["roofline"]["peak"]
     p.close()
+    # a D = 2 plan whose DCT runs on the tensor cores, timed with them on and off
+    wt = tc_profile_workload()
+    row = {"workload": wt.name, "N": wt.N, "M": wt.M}
+    c_on = None
+    for key, mode in (("tensor_cores", 0), ("fp64_units", -1)):
+        pt = F.Plan(wt.support, wt.sizes, wt.nodes, tensor_dct=mode, **opts)
+        xt = torch.empty(pt.M, dtype=torch.float64, device="cuda")
+        pt.sample(wt.family, wt.params, xt)
+        ct = torch.empty(pt.N, dtype=torch.float64, device="cuda")
+        rep = pt.execute(xt, ct)
+        b = torch.empty(pt.info["R"], dtype=torch.float64, device="cuda")
+        rhs_ms = statistics.mean(_timed(lambda: F.fct_plan_rhs(pt.handle, xt, b), max(3, steps // 4), flush))
+        ms = statistics.mean(_timed(lambda: pt.execute(xt, ct, report=False), max(3, steps // 4), flush))
+        row[key] = {"ms_per_transform": ms, "value": wt.N / (ms / 1e3), "rhs_stage_ms": rhs_ms,
+                    "tensor_dct_grids": pt.info["tensor_dct_grids"], "status": rep["status"],
+                    "iterations": rep["iterations"]}
+        if mode == 0:
+            c_on = ct.cpu().numpy()
+        else:
+            row["rel_diff_on_off"] = float(np.linalg.norm(c_on - ct.cpu().numpy()) / np.linalg.norm(ct.cpu().numpy()))
+        pt.close()
+    out["tensor_dct_D2"] = row
     # sparse S^inf support at D = 100 (3 nonzero components per index), 10 D grids,
     # a polynomial on the support recovered (the check that holds at any size)
     D, d, N = 100, 9, 20_000

@@ -169,8 +169,11 @@ __device__ __forceinline__ float2 sq_part(float v, double scale) { return df_squ
 __device__ __forceinline__ double pzero_part(double) { return 0.0; }
 __device__ __forceinline__ float2 pzero_part(float2) { return make_float2(0.0f, 0.0f); }
 
-template <int NW, typename WT, typename PT>
-__device__ bool phase_end(Team& tm, const WT (*wpart)[NW], PT* part, int u0, int nk) {
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return df_add(a, b); }
+__device__ __forceinline__ float2 pzero(float2) { return make_float2(0.0f, 0.0f); }
+
+template <int NW, typename PT>
+__device__ bool phase_end(Team& tm, const PT (*wpart)[NW], PT* part, int u0, int nk) {
   __shared__ int s_ok2;
   __syncthreads();
   tm.epoch += 1;
@@ -178,7 +181,7 @@ __device__ bool phase_end(Team& tm, const WT (*wpart)[NW], PT* part, int u0, int
     if (static_cast<int>(threadIdx.x) < nk) {
       PT v = pzero(PT{});
 #pragma unroll
-      for (int w = 0; w < NW; ++w) v = padd(v, widen(wpart[threadIdx.x][w]));
+      for (int w = 0; w < NW; ++w) v = padd(v, wpart[threadIdx.x][w]);
       stcg(part + u0 + static_cast<int>(threadIdx.x) * tm.G, v);
     }
     __syncwarp();
@@ -248,6 +251,26 @@ __device__ __forceinline__ double warp0_sum(const double* part, int n) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Warp 0: double-float sum of n per-unit partials (hi, lo) in a fixed order,
+// on the FP32 pipe: 8 independent accumulators per lane (one per load slot of
+// a round) keep the dependent chain short; the result (every lane) is the
+// pair's FP64 value.
+__device__ __forceinline__ double warp0_sum(const float2* part, int n) {
+  float2 acc[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) acc[j] = make_float2(0.0f, 0.0f);
+  for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
+    float2 t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = df_add(acc[j], t[j]);
+  }
+  const float2 s = df_add(df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])),
+                          df_add(df_add(acc[4], acc[5]), df_add(acc[6], acc[7])));
+  return widen(warp_sum(s));
 }
 
 // Warp 0: FP64 pair sums of n partials in a fixed order (lane 0 holds the result).

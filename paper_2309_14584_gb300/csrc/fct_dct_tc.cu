@@ -20,8 +20,8 @@
 // s + t = 7, about 2^-56 of sum_j |C[k][j]| |x[j]| per output.
 //
 // Kernels, per pass:
-//   tc_split_kernel  one thread per fibre: the fibre's exponent, then its 8
-//                    digit slices written as BF16 tiles in the layout the
+//   tc_exp_kernel,   the fibres' exponents (one warp per fibre), then their 8
+//   tc_digit_kernel  digit slices written as BF16 tiles in the layout the
 //                    tensor cores read (K-major, 8 x 16-byte core matrices);
 //   tc_gemm_kernel   one CTA of 128 threads per 128 x 64 output tile: warp 0
 //                    streams the A and B slices of each K step into shared
@@ -138,13 +138,54 @@ __device__ __forceinline__ double scale2(double v, int e) {
          __longlong_as_double(static_cast<long long>(e - h + 1023) << 52);
 }
 
+// (H 2^28 + L) 2^E, correctly rounded to FP64 with integer instructions only
+// (GB300's FP64 pipe is narrow; the epilogue converts every output once).
+// Exponents outside the normal range take the FP64 route, whose result is
+// the same correctly rounded value.
+__device__ __forceinline__ double combine_to_double(long long H, long long L, int E) {
+  const __int128 v = (static_cast<__int128>(H) << 28) + static_cast<__int128>(L);
+  if (v == 0) return 0.0;
+  const unsigned long long sign = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned __int128 av = v < 0 ? static_cast<unsigned __int128>(-v) : static_cast<unsigned __int128>(v);
+  const unsigned long long whi = static_cast<unsigned long long>(av >> 64);
+  const unsigned long long wlo = static_cast<unsigned long long>(av);
+  int msb = whi ? 127 - __clzll(static_cast<long long>(whi)) : 63 - __clzll(static_cast<long long>(wlo));
+  unsigned long long mant;
+  const int sh = msb - 52;
+  if (sh <= 0) {
+    mant = wlo << (-sh);
+  } else {
+    const unsigned __int128 m = av >> sh;
+    const unsigned __int128 rem = av - (m << sh);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    mant = static_cast<unsigned long long>(m);
+    if (rem > half || (rem == half && (mant & 1ull))) {
+      mant += 1ull;
+      if (mant == (1ull << 53)) {
+        mant >>= 1;
+        msb += 1;
+      }
+    }
+  }
+  const int bexp = msb + E + 1023;  // the value is mant 2^(msb - 52 + E), mant in [2^52, 2^53)
+  if (bexp <= 0 || bexp >= 2047)
+    return scale2(fma(static_cast<double>(L), 0x1p-28, static_cast<double>(H)), E + 28);
+  return __longlong_as_double(static_cast<long long>(sign | (static_cast<unsigned long long>(bexp) << 52) |
+                                                     (mant & ((1ull << 52) - 1))));
+}
+
 __device__ __forceinline__ const double* tc_src(int sel, const double* samples, const double* y0, const double* y1) {
   return sel == 0 ? samples : (sel == 1 ? y0 : y1);
 }
 
 // ---------------------------------------------------------------------------
-// Split: one thread per fibre c (64 per block = one N tile): exponent, then
-// the digit slices of x[c][j] for every K step, written as BF16 tiles.
+// Split, in two kernels per pass:
+//   tc_exp_kernel    one warp per fibre: the power of two above the fibre's
+//                    largest magnitude (bits of the magnitudes, no FP64 op);
+//   tc_digit_kernel  one thread per fibre and 8-element chunk: the 8 digit
+//                    slices of x[c][j], written as 16-byte rows of the BF16
+//                    tiles (consecutive threads: consecutive fibres).
+// Fibres beyond ncols and elements beyond n are zero.
 // ---------------------------------------------------------------------------
 struct SplitArgs {
   const TcGridPass* gp;
@@ -156,77 +197,89 @@ struct SplitArgs {
   int32_t* f;            // column exponents
 };
 
-__global__ void __launch_bounds__(kTcN) tc_split_kernel(const SplitArgs a) {
+__device__ __forceinline__ int64_t fibre_start(const TcGridPass& g, int c) {
+  const int p = c / g.post, q = c - (c / g.post) * g.post;
+  return static_cast<int64_t>(p) * g.n * g.post + q;
+}
+
+// block = 64 fibres of one N tile (two per warp in turn)
+__global__ void __launch_bounds__(256) tc_exp_kernel(const SplitArgs a) {
   const int gi = a.tasks[2 * blockIdx.x], nt = a.tasks[2 * blockIdx.x + 1];
   const TcGridPass g = a.gp[gi];
-  const int r = threadIdx.x;  // row of the B tile
+  const double* x = tc_src(g.in_sel, a.samples, a.y0, a.y1) + g.base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int r = warp; r < kTcN; r += 8) {
+    const int c = nt * kTcN + r;
+    unsigned long long mbits = 0;
+    if (c < g.ncols) {
+      const int64_t c0 = fibre_start(g, c);
+      for (int j = lane; j < g.n; j += 32) {
+        const unsigned long long bits =
+            static_cast<unsigned long long>(__double_as_longlong(ldcg(x + c0 + static_cast<int64_t>(j) * g.post))) &
+            0x7FFFFFFFFFFFFFFFull;
+        mbits = bits > mbits ? bits : mbits;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mbits, o);
+      mbits = t > mbits ? t : mbits;
+    }
+    if (lane == 0) {
+      int e = 0;
+      if (mbits >= 0x7FF0000000000000ull) {
+        e = kTcNonFinite;
+      } else if (mbits != 0) {
+        int bexp = static_cast<int>(mbits >> 52);
+        if (bexp == 0) bexp = 1 - (__clzll(static_cast<long long>(mbits)) - 11);  // subnormal maximum
+        e = bexp - 1022;  // max < 2^e (the frexp convention)
+      }
+      a.f[g.f_off + c] = e;
+    }
+  }
+}
+
+// block = 64 fibres x 4 chunks of 8 elements; grid.y walks the chunks
+__global__ void __launch_bounds__(256) tc_digit_kernel(const SplitArgs a) {
+  const int gi = a.tasks[2 * blockIdx.x], nt = a.tasks[2 * blockIdx.x + 1];
+  const TcGridPass g = a.gp[gi];
+  const int r = threadIdx.x & (kTcN - 1);
+  const int h = blockIdx.y * 4 + (threadIdx.x >> 6);  // 8-element chunk
+  if (h >= 2 * g.ksteps) return;
   const int c = nt * kTcN + r;
   const double* x = tc_src(g.in_sel, a.samples, a.y0, a.y1) + g.base;
-  const bool valid = c < g.ncols;
-  int64_t col0 = 0;
-  if (valid) {
-    const int p = c / g.post, q = c - (c / g.post) * g.post;
-    col0 = static_cast<int64_t>(p) * g.n * g.post + q;
-  }
-  // exponent of the fibre: max |x| by the bits of its magnitude
-  unsigned long long mbits = 0;
-  bool finite = true;
-  if (valid) {
-    for (int j = 0; j < g.n; ++j) {
-      const unsigned long long bits =
-          static_cast<unsigned long long>(__double_as_longlong(ldcg(x + col0 + static_cast<int64_t>(j) * g.post))) &
-          0x7FFFFFFFFFFFFFFFull;
-      if (bits >= 0x7FF0000000000000ull) finite = false;
-      mbits = bits > mbits ? bits : mbits;
-    }
-  }
-  int e = 0;
-  if (!finite) {
-    e = kTcNonFinite;
-  } else if (mbits != 0) {
-    int bexp = static_cast<int>(mbits >> 52);
-    if (bexp == 0) {  // subnormal maximum: exponent from the leading bit of the fraction
-      bexp = 1 - (__clzll(static_cast<long long>(mbits)) - 11);
-    }
-    e = bexp - 1022;  // max < 2^e, the frexp convention
-  }
-  a.f[g.f_off + c] = e;
-  // digit slices, 8 consecutive k of one row per 16-byte store
-  unsigned char* bt = a.b + g.b_off + static_cast<int64_t>(nt) * g.ksteps * kTcBStep;
-  const int off_r = (r / 8) * 256 + (r % 8) * 16;
-  for (int h = 0; h < 2 * g.ksteps; ++h) {
-    uint32_t packed[kTcSlices][4];
+  const int e = ldcg(a.f + g.f_off + c);
+  const bool live = c < g.ncols && e != kTcNonFinite;
+  const int64_t c0 = live ? fibre_start(g, c) : 0;
+  uint32_t packed[kTcSlices][4];
 #pragma unroll
-    for (int i = 0; i < 8; i += 2) {
-      int32_t dg[2][kTcSlices];
+  for (int i = 0; i < 8; i += 2) {
+    int32_t dg[2][kTcSlices];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int j = 8 * h + i + u;
-        long long v = 0;
-        if (valid && finite && j < g.n && mbits != 0)
-          v = __double2ll_rn(scale2(ldcg(x + col0 + static_cast<int64_t>(j) * g.post), 56 - e));
+    for (int u = 0; u < 2; ++u) {
+      const int j = 8 * h + i + u;
+      long long v = 0;
+      if (live && j < g.n) v = __double2ll_rn(scale2(ldcg(x + c0 + static_cast<int64_t>(j) * g.post), 56 - e));
 #pragma unroll
-        for (int t = kTcSlices - 1; t >= 1; --t) {
-          const long long qd = (v + 64) >> 7;
-          dg[u][t] = static_cast<int32_t>(v - qd * 128);
-          v = qd;
-        }
-        dg[u][0] = static_cast<int32_t>(v);
+      for (int t = kTcSlices - 1; t >= 1; --t) {
+        const long long qd = (v + 64) >> 7;
+        dg[u][t] = static_cast<int32_t>(v - qd * 128);
+        v = qd;
       }
-#pragma unroll
-      for (int t = 0; t < kTcSlices; ++t) {
-        const uint32_t lo = __float_as_uint(static_cast<float>(dg[0][t])) >> 16;
-        const uint32_t hi = __float_as_uint(static_cast<float>(dg[1][t])) >> 16;
-        packed[t][i / 2] = lo | (hi << 16);
-      }
+      dg[u][0] = static_cast<int32_t>(v);
     }
-    const int ks = h / 2, half = h % 2;
 #pragma unroll
     for (int t = 0; t < kTcSlices; ++t) {
-      uint4* dst = reinterpret_cast<uint4*>(bt + static_cast<int64_t>(ks) * kTcBStep + t * kTcBTile + off_r + half * 128);
-      *dst = make_uint4(packed[t][0], packed[t][1], packed[t][2], packed[t][3]);
+      const uint32_t lo = __float_as_uint(static_cast<float>(dg[0][t])) >> 16;
+      const uint32_t hi = __float_as_uint(static_cast<float>(dg[1][t])) >> 16;
+      packed[t][i / 2] = lo | (hi << 16);
     }
   }
+  unsigned char* bt = a.b + g.b_off + (static_cast<int64_t>(nt) * g.ksteps + h / 2) * kTcBStep;
+  const int off = (r / 8) * 256 + (h % 2) * 128 + (r % 8) * 16;
+#pragma unroll
+  for (int t = 0; t < kTcSlices; ++t)
+    *reinterpret_cast<uint4*>(bt + t * kTcBTile + off) = make_uint4(packed[t][0], packed[t][1], packed[t][2], packed[t][3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,7 +422,7 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
           for (int grp = 0; grp < 4; ++grp) H = (H << 7) + __float2ll_rn(__uint_as_float(v[grp][i]));
 #pragma unroll
           for (int grp = 4; grp < kTcSlices; ++grp) L = (L << 7) + __float2ll_rn(__uint_as_float(v[grp][i]));
-          y = scale2(fma(static_cast<double>(L), 0x1p-28, static_cast<double>(H)), ek + fc - 35);
+          y = combine_to_double(H, L, ek + fc - 63);
         }
         const int p = c / g.post, q = c - (c / g.post) * g.post;
         stcg(out + static_cast<int64_t>(p) * g.n * g.post + static_cast<int64_t>(k) * g.post + q, y);
@@ -456,7 +509,10 @@ fct_status tc_run(const TcHost& T, const TcDevice& D, const TcWork& Wk, const do
     const int ng = T.gemm_off[p + 1] - T.gemm_off[p];
     if (ns > 0) {
       SplitArgs sa{D.gp, D.split_tasks + 2 * T.split_off[p], samples, y0, y1, Wk.b, Wk.f};
-      tc_split_kernel<<<ns, kTcN, 0, st>>>(sa);
+      tc_exp_kernel<<<ns, 256, 0, st>>>(sa);
+      // chunks of 8 elements: 2 per K step, 4 per block row of the grid
+      const unsigned gy = static_cast<unsigned>((2 * T.max_ksteps + 3) / 4);
+      tc_digit_kernel<<<dim3(ns, gy), 256, 0, st>>>(sa);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return tc_cuda_fail(e, "tensor-core split launch");
     }

@@ -487,6 +487,16 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   if (o.plan_build < 0 || o.plan_build > 2) return fail(FCT_ERR_INVALID_ARG, "plan_build must be 0, 1 or 2");
   const bool on_device = o.plan_build != FCT_PLAN_BUILD_HOST;
 
+  // Plan construction runs on a stream of its own and synchronises only that
+  // stream, so plans can be built while other streams keep the device busy
+  // (e.g. a serving launch, when it leaves SMs free).
+  cudaStream_t cs = nullptr;
+  ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (ce != cudaSuccess) return cuda_fail(ce, "plan stream");
+  struct StreamGuard {
+    cudaStream_t s;
+    ~StreamGuard() { cudaStreamDestroy(s); }
+  } stream_guard{cs};
   auto* P = new fct_plan_s();
   P->opt = o;
   std::string err;
@@ -529,7 +539,8 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   }
   DeviceTables DT;  // device-built tables (scratch, freed on return)
   if (on_device) {
-    s = build_device_tables(&H, support, sizes, nodes, o.grid_kind, workers, wave, o.entries_per_lane, &epl, &DT);
+    s = build_device_tables(&H, support, sizes, nodes, o.grid_kind, workers, wave, o.entries_per_lane, &epl, &DT,
+                            cs);
     if (s != FCT_OK) {
       delete P;
       return s;
@@ -738,13 +749,13 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   }
   auto up = [&](void* dst, const void* src, size_t bytes) -> cudaError_t {
     if (bytes == 0) return cudaSuccess;
-    return cudaMemcpy(dst, src, bytes, on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice);
+    return cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDefault : cudaMemcpyHostToDevice, cs);
   };
   cudaError_t ue = cudaSuccess;
   auto chk = [&](cudaError_t x) {
     if (ue == cudaSuccess) ue = x;
   };
-  chk(cudaMemset(P->ls, 0, sizeof(LaunchState)));
+  chk(cudaMemsetAsync(P->ls, 0, sizeof(LaunchState), cs));
   chk(up(d_pass, H.pass_chunk_off.data(), sizeof(int32_t) * H.pass_chunk_off.size()));
   chk(up(d_chunks, H.dct_chunks.data(), sizeof(DctChunk) * H.dct_chunks.size()));
   chk(up(d_mats, H.dct_mats.data(), sizeof(double) * H.dct_mats.size()));
@@ -800,11 +811,11 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   if (ue == cudaSuccess && s == FCT_OK) s = choose_shape(P);
   if (ue == cudaSuccess && s == FCT_OK) chk(up(P->dp, &hp, sizeof(DevPlan)));
   if (ue == cudaSuccess && s == FCT_OK && nnodes > 0) {
-    cheb_table_kernel<<<static_cast<unsigned>((nnodes + 127) / 128), 128>>>(P->d_node_pos, static_cast<int>(nnodes),
-                                                                           P->dmax, P->d_ttab);
+    cheb_table_kernel<<<static_cast<unsigned>((nnodes + 127) / 128), 128, 0, cs>>>(
+        P->d_node_pos, static_cast<int>(nnodes), P->dmax, P->d_ttab);
     chk(cudaGetLastError());
-    chk(cudaDeviceSynchronize());
   }
+  chk(cudaStreamSynchronize(cs));
   if (ue != cudaSuccess || s != FCT_OK) {
     P->tables.reset();
     delete P;

@@ -99,6 +99,7 @@ struct TcHost {
   std::vector<uint16_t> a_bits;           // BF16 bits of every A slice
   std::vector<int32_t> a_exp;             // row exponents
   int64_t b_bytes = 0;                    // B workspace (largest pass)
+  int32_t max_ksteps = 0;                 // most K steps of any pass
   int64_t f_count = 0;                    // column-exponent workspace (largest pass)
   // the solver's DCT for plans run with the tensor-core passes: passes of the
   // grids left to the FP64 units, and a last pass that reads the finished
@@ -304,6 +305,7 @@ struct DeviceTables {
   int32_t* crow = nullptr;     // [K N] coefficient-major
   double* wcm = nullptr;
   float* wcm32 = nullptr;
+  void* stream = nullptr;      // cudaStream_t of the build: allocation and release are ordered on it
   void release();
   ~DeviceTables() { release(); }
 };
@@ -313,9 +315,12 @@ struct DeviceTables {
 // false)).  Chooses the entries per lane as the host path does
 // (pick_entries_per_lane), fills H->R, H->rowptr and H->rowsrc in the device
 // row order, and out->rowbase / out->rowk as final_pass_rows would.
+// Every launch, copy, allocation and release of the build is ordered on
+// `stream` (a cudaStream_t); the call synchronises that stream only, so a plan
+// can be built while other streams (a serving launch) keep the device busy.
 fct_status build_device_tables(HostTables* H, const uint16_t* support, const int32_t* sizes, const double* nodes,
                                int grid_kind, int workers, int64_t wave, int fixed_epl, int* epl,
-                               DeviceTables* out);
+                               DeviceTables* out, void* stream);
 // Copies col, wcsr, crow and the coefficient-major values back into H.
 fct_status download_device_tables(const DeviceTables& T, HostTables* H);
 

@@ -433,22 +433,22 @@ fct_status cuda_err(cudaError_t e, const char* what) {
 }
 
 // Exclusive scan of n int32 (in place allowed); the total is left in *total.
-void exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* partial, int32_t* total) {
+void exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* partial, int32_t* total, cudaStream_t st) {
   const int64_t nb = std::max<int64_t>(1, (n + kScanTile - 1) / kScanTile);
-  scan_reduce_kernel<<<static_cast<unsigned>(nb), kScanThreads>>>(in, n, partial);
-  scan_partials_kernel<<<1, kScanThreads>>>(partial, nb, total);
-  scan_apply_kernel<<<static_cast<unsigned>(nb), kScanThreads>>>(in, n, partial, out);
+  scan_reduce_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, partial);
+  scan_partials_kernel<<<1, kScanThreads, 0, st>>>(partial, nb, total);
+  scan_apply_kernel<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, partial, out);
 }
 
 // Stable LSD radix sort of (key, val) by the low `bits` bits of key (keys are
 // non-negative).  The sorted pairs end in (*k, *v); the other pair is scratch.
 void radix_sort(int32_t** k, int32_t** v, int32_t** k2, int32_t** v2, int64_t n, int bits, int32_t* ghist,
-                int32_t* partial, int32_t* total) {
+                int32_t* partial, int32_t* total, cudaStream_t st) {
   const int64_t nblk = (n + kSortTile - 1) / kSortTile;
   for (int shift = 0; shift < bits; shift += 8) {
-    radix_hist_kernel<<<static_cast<unsigned>(nblk), kSortThreads>>>(*k, n, shift, ghist, nblk);
-    exclusive_scan(ghist, ghist, 256 * nblk, partial, total);
-    radix_scatter_kernel<<<static_cast<unsigned>(nblk), kSortThreads>>>(*k, *v, n, shift, ghist, nblk, *k2, *v2);
+    radix_hist_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(*k, n, shift, ghist, nblk);
+    exclusive_scan(ghist, ghist, 256 * nblk, partial, total, st);
+    radix_scatter_kernel<<<static_cast<unsigned>(nblk), kSortThreads, 0, st>>>(*k, *v, n, shift, ghist, nblk, *k2, *v2);
     std::swap(*k, *k2);
     std::swap(*v, *v2);
   }
@@ -457,14 +457,20 @@ void radix_sort(int32_t** k, int32_t** v, int32_t** k2, int32_t** v2, int64_t n,
 }  // namespace
 
 void DeviceTables::release() {
-  if (mem) cudaFree(mem);
+  if (mem) {
+    // stream-ordered: no device-wide synchronisation, so a plan can be built
+    // while other work (a serving launch) runs
+    cudaFreeAsync(mem, static_cast<cudaStream_t>(stream));
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  }
   mem = nullptr;
 }
 
 fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const int32_t* sizes, const double* nodes,
                                int grid_kind, int workers, int64_t wave, int fixed_epl, int* epl_out,
-                               DeviceTables* out) {
+                               DeviceTables* out, void* stream) {
   HostTables& H = *Hp;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int D = H.D, K = H.K;
   const int64_t N = H.N, KN = static_cast<int64_t>(K) * N;
   out->release();
@@ -533,9 +539,10 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   size_t total = 0;
   for (auto& pc : pieces) total += a256(pc.bytes);
   void* mem = nullptr;
-  cudaError_t e = cudaMalloc(&mem, total);
-  if (e != cudaSuccess) return cuda_err(e, "cudaMalloc(device table build)");
+  cudaError_t e = cudaMallocAsync(&mem, total, st);
+  if (e != cudaSuccess) return cuda_err(e, "cudaMallocAsync(device table build)");
   out->mem = mem;
+  out->stream = stream;
   {
     size_t off = 0;
     for (auto& pc : pieces) {
@@ -549,26 +556,26 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   auto chk = [&](cudaError_t x) {
     if (ue == cudaSuccess) ue = x;
   };
-  chk(cudaMemcpy(d_support, support, sizeof(uint16_t) * N * D, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(d_sizes, sizes, sizeof(int32_t) * K * D, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(d_strides, strides.data(), sizeof(int32_t) * K * D, cudaMemcpyHostToDevice));
-  if (nodes) chk(cudaMemcpy(d_nodes, nodes, sizeof(double) * K * D, cudaMemcpyHostToDevice));
-  chk(cudaMemcpy(d_offsets, H.offsets.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice));
+  chk(cudaMemcpyAsync(d_support, support, sizeof(uint16_t) * N * D, cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(d_sizes, sizes, sizeof(int32_t) * K * D, cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(d_strides, strides.data(), sizeof(int32_t) * K * D, cudaMemcpyHostToDevice, st));
+  if (nodes) chk(cudaMemcpyAsync(d_nodes, nodes, sizeof(double) * K * D, cudaMemcpyHostToDevice, st));
+  chk(cudaMemcpyAsync(d_offsets, H.offsets.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice, st));
   if (static_cast<int>(H.gfinal.size()) != K) {
     out->release();
     return fail(FCT_ERR_INVALID_ARG, "internal: device table build needs the DCT set-up");
   }
-  chk(cudaMemcpy(d_gfinal, H.gfinal.data(), sizeof(GridFinal) * K, cudaMemcpyHostToDevice));
+  chk(cudaMemcpyAsync(d_gfinal, H.gfinal.data(), sizeof(GridFinal) * K, cudaMemcpyHostToDevice, st));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build upload");
   }
 
   // 0. nonzero components; 1. fold
-  nz_count_kernel<<<elem_blocks(N + 1), kElemThreads>>>(N, D, d_support, d_nzoff);
-  exclusive_scan(d_nzoff, d_nzoff, N + 1, d_part, d_small);
-  nz_fill_kernel<<<elem_blocks(N), kElemThreads>>>(N, D, d_support, d_nzoff, d_pairs);
-  fold_kernel<<<elem_blocks(KN), kElemThreads>>>(KN, N, D, d_nzoff, d_pairs, d_sizes, d_strides,
+  nz_count_kernel<<<elem_blocks(N + 1), kElemThreads, 0, st>>>(N, D, d_support, d_nzoff);
+  exclusive_scan(d_nzoff, d_nzoff, N + 1, d_part, d_small, st);
+  nz_fill_kernel<<<elem_blocks(N), kElemThreads, 0, st>>>(N, D, d_support, d_nzoff, d_pairs);
+  fold_kernel<<<elem_blocks(KN), kElemThreads, 0, st>>>(KN, N, D, d_nzoff, d_pairs, d_sizes, d_strides,
                                                  nodes ? d_nodes : nullptr, d_offsets,
                                                  grid_kind == FCT_GRID_FIRST_KIND ? 1 : 0, d_k0, d_v0, d_weight);
   // 2. stable sort by the global bin key (keys < M)
@@ -576,15 +583,16 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   while (bits < 31 && ((H.M - 1) >> bits) > 0) ++bits;
   if (bits == 0) bits = 1;
   int32_t *sk = d_k0, *sv = d_v0, *ak = d_k1, *av = d_v1;
-  radix_sort(&sk, &sv, &ak, &av, KN, bits, d_ghist, d_part, d_small);
+  radix_sort(&sk, &sv, &ak, &av, KN, bits, d_ghist, d_part, d_small, st);
   // 3. compaction: flags into ak, scanned in place
-  row_flag_kernel<<<elem_blocks(KN), kElemThreads>>>(sk, KN, ak);
-  exclusive_scan(ak, ak, KN, d_part, d_small);
-  csr_fill_kernel<<<elem_blocks(KN), kElemThreads>>>(sk, sv, ak, KN, N, d_weight, d_rowptr0, d_rowsrc0, d_rowgrid0,
+  row_flag_kernel<<<elem_blocks(KN), kElemThreads, 0, st>>>(sk, KN, ak);
+  exclusive_scan(ak, ak, KN, d_part, d_small, st);
+  csr_fill_kernel<<<elem_blocks(KN), kElemThreads, 0, st>>>(sk, sv, ak, KN, N, d_weight, d_rowptr0, d_rowsrc0, d_rowgrid0,
                                                      d_col0, d_wcsr0, d_crow0);
   chk(cudaGetLastError());
   int32_t nflags = 0;  // the flag scan's total: the number of rows
-  chk(cudaMemcpy(&nflags, d_small, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  chk(cudaMemcpyAsync(&nflags, d_small, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build (fold, sort, compaction)");
@@ -596,10 +604,11 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   }
 
   // entries per lane from the lane-class histogram
-  chk(cudaMemset(d_small, 0, sizeof(int32_t) * 32));
-  lane_class_kernel<<<elem_blocks(R), kElemThreads>>>(d_rowptr0, R, d_small);
+  chk(cudaMemsetAsync(d_small, 0, sizeof(int32_t) * 32, st));
+  lane_class_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(d_rowptr0, R, d_small);
   int32_t hist[kClassCounters];
-  chk(cudaMemcpy(hist, d_small, sizeof(hist), cudaMemcpyDeviceToHost));
+  chk(cudaMemcpyAsync(hist, d_small, sizeof(hist), cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build (lane classes)");
@@ -613,17 +622,17 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   // 4. device row order: one stable pass keyed by the lane class (reuses
   // the sort buffers: the sorted pairs are no longer needed)
   int32_t *rk = d_k0, *rv = d_v0, *rk2 = d_k1, *rv2 = d_v1;
-  row_class_key_kernel<<<elem_blocks(R), kElemThreads>>>(d_rowptr0, R, epl, rk, rv);
-  radix_sort(&rk, &rv, &rk2, &rv2, R, 3, d_ghist, d_part, d_small);
+  row_class_key_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(d_rowptr0, R, epl, rk, rv);
+  radix_sort(&rk, &rv, &rk2, &rv2, R, 3, d_ghist, d_part, d_small, st);
   const int32_t* order = rv;
-  row_perm_kernel<<<elem_blocks(R), kElemThreads>>>(order, R, d_rowptr0, d_rowsrc0, d_rowgrid0, out->rowptr, d_inv,
+  row_perm_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(order, R, d_rowptr0, d_rowsrc0, d_rowgrid0, out->rowptr, d_inv,
                                                     d_rowsrc, out->rowgrid);
-  exclusive_scan(out->rowptr, out->rowptr, R, d_part, d_small);
-  set_int_kernel<<<1, 1>>>(out->rowptr + R, static_cast<int32_t>(KN));
-  entry_perm_kernel<<<elem_blocks(KN), kElemThreads>>>(out->rowptr, R, order, d_rowptr0, d_col0, d_wcsr0, KN,
+  exclusive_scan(out->rowptr, out->rowptr, R, d_part, d_small, st);
+  set_int_kernel<<<1, 1, 0, st>>>(out->rowptr + R, static_cast<int32_t>(KN));
+  entry_perm_kernel<<<elem_blocks(KN), kElemThreads, 0, st>>>(out->rowptr, R, order, d_rowptr0, d_col0, d_wcsr0, KN,
                                                        out->col, out->wcsr, out->wcsr32);
-  coef_table_kernel<<<elem_blocks(KN), kElemThreads>>>(d_crow0, d_inv, d_weight, KN, out->crow, out->wcm32);
-  final_rows_kernel<<<elem_blocks(R), kElemThreads>>>(R, d_rowsrc, out->rowgrid, d_offsets, d_gfinal, out->rowbase,
+  coef_table_kernel<<<elem_blocks(KN), kElemThreads, 0, st>>>(d_crow0, d_inv, d_weight, KN, out->crow, out->wcm32);
+  final_rows_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(R, d_rowsrc, out->rowgrid, d_offsets, d_gfinal, out->rowbase,
                                                       out->rowk);
   chk(cudaGetLastError());
 
@@ -631,8 +640,9 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   H.rowptr.assign(R + 1, 0);
   H.rowsrc.assign(R, 0);
   H.rowgrid.clear();  // stays on the device (out->rowgrid)
-  chk(cudaMemcpy(H.rowptr.data(), out->rowptr, sizeof(int32_t) * (R + 1), cudaMemcpyDeviceToHost));
-  chk(cudaMemcpy(H.rowsrc.data(), d_rowsrc, sizeof(int32_t) * R, cudaMemcpyDeviceToHost));
+  chk(cudaMemcpyAsync(H.rowptr.data(), out->rowptr, sizeof(int32_t) * (R + 1), cudaMemcpyDeviceToHost, st));
+  chk(cudaMemcpyAsync(H.rowsrc.data(), d_rowsrc, sizeof(int32_t) * R, cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
   if (ue != cudaSuccess) {
     out->release();
     return cuda_err(ue, "device table build (row order)");
@@ -645,6 +655,7 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
 }
 
 fct_status download_device_tables(const DeviceTables& T, HostTables* Hp) {
+  const cudaStream_t st = static_cast<cudaStream_t>(T.stream);
   HostTables& H = *Hp;
   const int64_t KN = static_cast<int64_t>(H.K) * H.N;
   H.col.resize(KN);
@@ -655,10 +666,11 @@ fct_status download_device_tables(const DeviceTables& T, HostTables* Hp) {
   auto chk = [&](cudaError_t x) {
     if (ue == cudaSuccess) ue = x;
   };
-  chk(cudaMemcpy(H.col.data(), T.col, sizeof(int32_t) * KN, cudaMemcpyDeviceToHost));
-  chk(cudaMemcpy(H.wcsr.data(), T.wcsr, sizeof(double) * KN, cudaMemcpyDeviceToHost));
-  chk(cudaMemcpy(H.crow.data(), T.crow, sizeof(int32_t) * KN, cudaMemcpyDeviceToHost));
-  chk(cudaMemcpy(H.weight.data(), T.wcm, sizeof(double) * KN, cudaMemcpyDeviceToHost));
+  chk(cudaMemcpyAsync(H.col.data(), T.col, sizeof(int32_t) * KN, cudaMemcpyDeviceToHost, st));
+  chk(cudaMemcpyAsync(H.wcsr.data(), T.wcsr, sizeof(double) * KN, cudaMemcpyDeviceToHost, st));
+  chk(cudaMemcpyAsync(H.crow.data(), T.crow, sizeof(int32_t) * KN, cudaMemcpyDeviceToHost, st));
+  chk(cudaMemcpyAsync(H.weight.data(), T.wcm, sizeof(double) * KN, cudaMemcpyDeviceToHost, st));
+  chk(cudaStreamSynchronize(st));
   return ue == cudaSuccess ? FCT_OK : cuda_err(ue, "device table download");
 }
 

@@ -668,6 +668,7 @@ fct_status build_tc_host(HostTables* Hp, const int32_t* sizes, int grid_kind, in
       g.post = static_cast<int32_t>(post);
       g.ncols = static_cast<int32_t>(Tl / g.n);
       g.ksteps = (g.n + kTcK - 1) / kTcK;
+      T->max_ksteps = std::max(T->max_ksteps, g.ksteps);
       g.mtiles = (g.n + kTcM - 1) / kTcM;
       g.ntiles = (g.ncols + kTcN - 1) / kTcN;
       g.a_off = a_off_of[g.n];

@@ -484,12 +484,16 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     v = warp_sum(v);
     if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
   };
-  auto flush = [&](double* part, int u0, int nk) {
+  // per-unit partials: FP64 (FP64 vectors) or double-float pairs (FP32
+  // vectors), in the 8-byte slots of part_r / part_c
+  PT* const part_r = reinterpret_cast<PT*>(P.part_r);
+  PT* const part_c = reinterpret_cast<PT*>(P.part_c);
+  auto flush = [&](PT* part, int u0, int nk) {
     __syncthreads();
     if (threadIdx.x < nk) {
-      double v = 0.0;
+      PT v = pzero(PT{});
 #pragma unroll
-      for (int w2 = 0; w2 < NW; ++w2) v += widen(wpart[threadIdx.x][w2]);
+      for (int w2 = 0; w2 < NW; ++w2) v = padd(v, wpart[threadIdx.x][w2]);
       stcg(part + u0 + threadIdx.x * tm.G, v);
     }
     __syncthreads();
@@ -509,7 +513,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
         if (u < nru) gather_a(u, 0, &as, &ap, &row, &lead);
       } else {
         double gnew = 1.0;
-        if (!first) gnew = warp0_sum(P.part_c, ncc);
+        if (!first) gnew = widen(warp0_sum(part_c, ncc));
         if (threadIdx.x == 0) {
           int c = 0;
           double bt = 0.0;
@@ -552,12 +556,12 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && u + tm.G < nru) {
-          flush(P.part_r, u0, kg);
+          flush(part_r, u0, kg);
           kg = 0;
           u0 = u + tm.G;
         }
       }
-      if (!phase_end<NW>(tm, wpart, P.part_r, u0, kg)) return false;
+      if (!phase_end<NW>(tm, wpart, part_r, u0, kg)) return false;
     }
     // ================= phase B: t = A^T q; {s, p} and x updated by the owner
     {
@@ -581,7 +585,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           t = coef_gather<V, WT, SV>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
         }
       } else {
-        const double dl = warp0_sum(P.part_r, nru);
+        const double dl = widen(warp0_sum(part_r, nru));
         if (threadIdx.x == 0) {
           int cc = 0;
           double al = 0.0;
@@ -618,12 +622,12 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
         }
         warp_part(kg, part);
         if (++kg == kUnitGroup && c + tm.G < ncc) {
-          flush(P.part_c, c0, kg);
+          flush(part_c, c0, kg);
           kg = 0;
           c0 = c + tm.G;
         }
       }
-      if (!phase_end<NW>(tm, wpart, P.part_c, c0, kg)) return false;
+      if (!phase_end<NW>(tm, wpart, part_c, c0, kg)) return false;
     }
     first = false;
   }

@@ -8,6 +8,7 @@ import torch
 
 import paper_2309_14584_gb300 as F
 import workloads as W
+from oracle import fct_oracle as O
 from paper_2309_14584_gb300.serving import ServingEngine, latency_summary
 
 pytestmark = pytest.mark.gpu
@@ -120,3 +121,32 @@ def test_teams_stay_while_a_long_job_runs():
     F.fct_server_destroy(srv)
     for p in ps + [pl]:
         p.close()
+
+
+def test_served_results_match_the_oracle():
+    """Gaussian-cosine requests over shapes of D = 2 .. 20, served in one
+    burst (several teams at once), each result against the oracle's
+    least-squares solution of the same seeded problem at the mixed-path bar."""
+    shapes = [W.make_workload(f"s{D}", 70 + D, D, d, 3 * D, 1, d + 1, W.FAMILY_GAUSSCOS, tol=1e-12, precision="mixed")
+              for D, d in ((2, 40), (3, 15), (4, 9), (6, 6), (12, 3), (20, 2))]
+    eng = ServingEngine(shapes, max_slots_per_shape=2, team_blocks=8, precision=F.FCT_MIXED, tol=1e-12,
+                        inner_tol=1e-4)
+    inputs = {}
+    for s, w in enumerate(shapes):
+        for v in range(2):
+            x = torch.empty(eng.plans[s].M, dtype=torch.float64, device="cuda")
+            eng.plans[s].sample(W.FAMILY_GAUSSCOS, W.gausscos_params(500 + 10 * s + v, w.D), x)
+            inputs[(s, v)] = x
+    torch.cuda.synchronize()
+    reqs = [(0.0, s, (s, v)) for v in range(2) for s in range(len(shapes))]
+    outs = [torch.empty(eng.plans[s].N, dtype=torch.float64, device="cuda") for _, s, _ in reqs]
+    res = eng.run(reqs, inputs, outs, timeout_s=120)
+    eng.close()
+    assert all(r["report"]["status"] == 0 for r in res)
+    for (t, s, (_, v)), o in zip(reqs, outs):
+        w = shapes[s]
+        params = W.gausscos_params(500 + 10 * s + v, w.D)
+        f = O.sample_lgrid(W.FAMILY_GAUSSCOS, params, w.support, w.sizes, w.nodes)
+        ref = O.fct(w.support, w.sizes, w.nodes, f, "qr")
+        err = float(np.linalg.norm(o.cpu().numpy() - ref) / np.linalg.norm(ref))
+        assert err <= 1e-10, (w.name, v, err)

@@ -17,6 +17,8 @@ class _FakePlan:
         self.handle = 1000 + _FakePlan.count
         n = int(np.asarray(support).shape[0])
         self.info = {"N": n, "M": 10 * n, "R": 3 * n}
+        # tables and one workspace, as the library reports them
+        self.info["device_bytes"] = 8.0 * (2 * 10 * n + 3 * 3 * n + 2 * n) + 4.0 * (3 * n + 3 * n)
 
     def clone(self):
         c = _FakePlan.__new__(_FakePlan)
@@ -191,3 +193,29 @@ def test_failed_job_report_reaches_the_summary(monkeypatch):
     summ = serving.latency_summary(res, [50] * 3)
     assert not summ["all_converged"]
     assert sorted(r["report"]["status"] for r in res) == [0, 0, 4]
+
+
+def test_lazy_plans_are_built_on_first_request_and_counted_cold(monkeypatch):
+    """lazy_plans: no plan exists before its shape's first request; that
+    request is reported cold, later ones of the shape are not, and clones are
+    made on demand within the budget."""
+    shapes = [_shape(100), _shape(200)]
+    srv = _FakeServer(2)
+    fake = types.SimpleNamespace(
+        Plan=_FakePlan,
+        fct_server_create=lambda *a: srv,
+        fct_server_submit=lambda s, plan, x, c: s.submit(plan, x, c),
+        fct_server_poll=lambda s, t: s.poll(t),
+        fct_server_destroy=lambda s: None,
+    )
+    monkeypatch.setattr(serving, "F", fake)
+    eng = serving.ServingEngine(shapes, hbm_budget_bytes=1e9, max_slots_per_shape=3, lazy_plans=True)
+    assert eng.plans == [None, None]
+    reqs = [(0.0, 1, "b"), (0.0, 1, "b"), (0.0, 1, "b"), (0.05, 0, "a")]
+    res = eng.run(reqs, {"a": "xa", "b": "xb"}, ["o0", "o1", "o2", "o3"], timeout_s=30)
+    assert res[0]["cold"] and res[3]["cold"]
+    assert not res[1]["cold"] and not res[2]["cold"]
+    assert eng.plans[0] is not None and eng.plans[1] is not None
+    assert len(eng.slots[1]) == 3          # base plan + two clones made on demand
+    assert set(eng.plan_build_s) == {0, 1}
+    assert eng.used_bytes <= eng.budget
