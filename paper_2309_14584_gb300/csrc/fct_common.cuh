@@ -152,6 +152,18 @@ __device__ __forceinline__ float2 warp_sum(float2 v) {
     v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
   return v;
 }
+// Warp sum of values held only by lanes that are multiples of lc (the lead
+// lanes of rows or coefficients with lc lanes each; the other lanes hold 0):
+// log2(32 / lc) shuffle levels instead of 5, in a fixed order.
+__device__ __forceinline__ double warp_sum_from(double v, int lc) {
+  for (int o = 16; o >= lc; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float2 warp_sum_from(float2 v, int lc) {
+  for (int o = 16; o >= lc; o >>= 1)
+    v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)));
+  return v;
+}
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double2 widen(double2 v) { return v; }
 __device__ __forceinline__ double widen(float2 v) { return static_cast<double>(v.x) + static_cast<double>(v.y); }

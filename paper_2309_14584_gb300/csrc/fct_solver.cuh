@@ -480,9 +480,14 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
   double gam = c0, best = c0;
   int it = 0, best_it = 0;
   bool first = true;
-  auto warp_part = [&](int kk, PT v) {
-    v = warp_sum(v);
+  // lead lanes of a unit sit at multiples of its lanes per row (coefficient)
+  auto warp_part = [&](int kk, PT v, int lc) {
+    v = warp_sum_from(v, lc);
     if (wk >= 0 && lane32 == 0) wpart[kk][warp] = v;
+  };
+  auto unit_lanes = [&](int u, int k) {
+    if (u < nwide) return 32;  // a wide row's sum sits on thread wk = 0 alone
+    return k < T.cachedA ? T.hdrA[5 * k + 2] : __ldg(P.ru_lanes + u);
   };
   // per-unit partials: FP64 (FP64 vectors) or double-float pairs (FP32
   // vectors), in the 8-byte slots of part_r / part_c
@@ -554,7 +559,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           stcg(q + row, qv);
           part = sq_part(qv, rs);
         }
-        warp_part(kg, part);
+        warp_part(kg, part, unit_lanes(u, k));
         if (++kg == kUnitGroup && u + tm.G < nru) {
           flush(part_r, u0, kg);
           kg = 0;
@@ -620,7 +625,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           stcg(x + m, static_cast<XT>(fma(static_cast<XT>(alpha), static_cast<XT>(pn), xo)));
           part = sq_part(sn, rs);
         }
-        warp_part(kg, part);
+        warp_part(kg, part, L);
         if (++kg == kUnitGroup && c + tm.G < ncc) {
           flush(part_c, c0, kg);
           kg = 0;
