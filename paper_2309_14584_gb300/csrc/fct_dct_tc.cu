@@ -202,40 +202,41 @@ __device__ __forceinline__ int64_t fibre_start(const TcGridPass& g, int c) {
   return static_cast<int64_t>(p) * g.n * g.post + q;
 }
 
-// block = 64 fibres of one N tile (two per warp in turn)
+// block = 64 fibres of one N tile x 4 groups of elements: thread (r, gq)
+// scans j = gq, gq + 4, ... of fibre r (consecutive threads read consecutive
+// fibres, so loads coalesce when the fibres are strided); the four partial
+// maxima meet in shared memory.
 __global__ void __launch_bounds__(256) tc_exp_kernel(const SplitArgs a) {
+  __shared__ unsigned long long smax[4][kTcN];
   const int gi = a.tasks[2 * blockIdx.x], nt = a.tasks[2 * blockIdx.x + 1];
   const TcGridPass g = a.gp[gi];
   const double* x = tc_src(g.in_sel, a.samples, a.y0, a.y1) + g.base;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int r = warp; r < kTcN; r += 8) {
-    const int c = nt * kTcN + r;
-    unsigned long long mbits = 0;
-    if (c < g.ncols) {
-      const int64_t c0 = fibre_start(g, c);
-      for (int j = lane; j < g.n; j += 32) {
-        const unsigned long long bits =
-            static_cast<unsigned long long>(__double_as_longlong(ldcg(x + c0 + static_cast<int64_t>(j) * g.post))) &
-            0x7FFFFFFFFFFFFFFFull;
-        mbits = bits > mbits ? bits : mbits;
-      }
+  const int r = threadIdx.x & (kTcN - 1), gq = threadIdx.x >> 6;
+  const int c = nt * kTcN + r;
+  unsigned long long mbits = 0;
+  if (c < g.ncols) {
+    const int64_t c0 = fibre_start(g, c);
+    for (int j = gq; j < g.n; j += 4) {
+      const unsigned long long bits =
+          static_cast<unsigned long long>(__double_as_longlong(ldcg(x + c0 + static_cast<int64_t>(j) * g.post))) &
+          0x7FFFFFFFFFFFFFFFull;
+      mbits = bits > mbits ? bits : mbits;
     }
+  }
+  smax[gq][r] = mbits;
+  __syncthreads();
+  if (gq == 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long t = __shfl_xor_sync(0xffffffffu, mbits, o);
-      mbits = t > mbits ? t : mbits;
+    for (int q = 1; q < 4; ++q) mbits = smax[q][r] > mbits ? smax[q][r] : mbits;
+    int e = 0;
+    if (mbits >= 0x7FF0000000000000ull) {
+      e = kTcNonFinite;
+    } else if (mbits != 0) {
+      int bexp = static_cast<int>(mbits >> 52);
+      if (bexp == 0) bexp = 1 - (__clzll(static_cast<long long>(mbits)) - 11);  // subnormal maximum
+      e = bexp - 1022;  // max < 2^e (the frexp convention)
     }
-    if (lane == 0) {
-      int e = 0;
-      if (mbits >= 0x7FF0000000000000ull) {
-        e = kTcNonFinite;
-      } else if (mbits != 0) {
-        int bexp = static_cast<int>(mbits >> 52);
-        if (bexp == 0) bexp = 1 - (__clzll(static_cast<long long>(mbits)) - 11);  // subnormal maximum
-        e = bexp - 1022;  // max < 2^e (the frexp convention)
-      }
-      a.f[g.f_off + c] = e;
-    }
+    a.f[g.f_off + c] = e;
   }
 }
 
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
   __shared__ __align__(8) unsigned long long bars[2 * kTcStages + 1];  // full[s], empty[s], done
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
+  __shared__ int s_fexp[kTcN];  // the tile's column exponents
   const int* task = a.tasks + 4 * blockIdx.x;
   const TcGridPass g = a.gp[task[0]];
   const int mt = task[1], nt = task[2];
@@ -326,6 +328,10 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), kTcTmemCols);
+  if (threadIdx.x < kTcN) {
+    const int c = nt * kTcN + static_cast<int>(threadIdx.x);
+    s_fexp[threadIdx.x] = c < g.ncols ? ldcg(a.f + g.f_off + c) : 0;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -409,7 +415,7 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
       for (int i = 0; i < 16; ++i) {
         const int c = nt * kTcN + cc * 16 + i;
         if (!krow || c >= g.ncols) continue;
-        const int fc = ldcg(a.f + g.f_off + c);
+        const int fc = s_fexp[cc * 16 + i];
         double y;
         if (fc == kTcNonFinite) {
           y = __longlong_as_double(0x7FF8000000000000ll);
@@ -417,11 +423,14 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
           // exact digit sums G_g (integers held in FP32), combined as
           // H = sum_{g<4} G_g 2^(7(3-g)), L = sum_{g>=4} G_g 2^(7(7-g)):
           // y = 2^(e_k + f_c - 35) (H + 2^-28 L)
+          // each sum is an integer below 2^27 in magnitude: exact as int32
           long long H = 0, L = 0;
 #pragma unroll
-          for (int grp = 0; grp < 4; ++grp) H = (H << 7) + __float2ll_rn(__uint_as_float(v[grp][i]));
+          for (int grp = 0; grp < 4; ++grp)
+            H = (H << 7) + static_cast<long long>(__float2int_rn(__uint_as_float(v[grp][i])));
 #pragma unroll
-          for (int grp = 4; grp < kTcSlices; ++grp) L = (L << 7) + __float2ll_rn(__uint_as_float(v[grp][i]));
+          for (int grp = 4; grp < kTcSlices; ++grp)
+            L = (L << 7) + static_cast<long long>(__float2int_rn(__uint_as_float(v[grp][i])));
           y = combine_to_double(H, L, ek + fc - 63);
         }
         const int p = c / g.post, q = c - (c / g.post) * g.post;
