@@ -978,6 +978,7 @@ def run_serving(args, F):
                 if key[1] != "poly" and shapes[s].N <= SERVING_CHECK_MAX_N:
                     served.setdefault(key, o.cpu().numpy())
     eng.close()
+    cold = run_serving_cold(args, F, shapes, inputs)
     checks = []
     for (s, v), c in sorted(served.items()):
         w = dataclasses.replace(shapes[s], params=W.gausscos_params(shapes[s].D * 1000 + v, shapes[s].D))
@@ -987,8 +988,44 @@ def run_serving(args, F):
                       f"to 1e-12 normal residual; grid counts by Algorithm 2 with kappa0 = {args.serving_kappa0}; "
                       f"served Gaussian-cosine results of shapes with N <= {SERVING_CHECK_MAX_N} at the highest "
                       "rate are compared with the CPU oracle",
-            "grid_selection_s": round(t_select, 2), "shapes": sel, "rates": out,
+            "grid_selection_s": round(t_select, 2), "shapes": sel, "rates": out, "cold_plans": cold,
             "team_blocks": args.serving_team_blocks, "check_results": checks}
+
+
+def run_serving_cold(args, F, shapes, inputs, rate=25.0, n_req=60):
+    """Plan-cache misses while serving: a fresh engine holds no plan; each
+    shape's plan is built when its first request is admitted (grid counts as
+    chosen by Algorithm 2 beforehand), while the serving launch runs on all
+    teams but one (the free SMs run the plan builder's kernels).  Cold
+    requests (their latency includes the plan build) are reported apart from
+    the warm ones of the same run."""
+    import numpy as np
+    import workloads as W
+    from paper_2309_14584_gb300.serving import ServingEngine
+    eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=args.serving_team_blocks,
+                        teams=max(1, 304 // args.serving_team_blocks - 1), lazy_plans=True, precision=F.FCT_MIXED,
+                        tol=1e-12, inner_tol=1e-4, max_iter=20000)
+    raw = W.serving_requests(9, n_req, rate, len(shapes), poly_fraction=0.0)
+    reqs = [(t, s, (s, ps % SERVING_VARIANTS)) for t, s, _, ps in raw]
+    outs = [torch_empty(shapes[s].N) for _, s, _ in reqs]
+    res = eng.run(reqs, inputs, outs, timeout_s=300)
+    builds = [1e3 * eng.plan_build_s[s] for s in sorted(eng.plan_build_s)]
+    eng.close()
+    cold = [1e3 * r["latency_s"] for r in res if r["cold"]]
+    warm = [1e3 * r["latency_s"] for r in res if not r["cold"]]
+    return {"requests": len(res), "rate_req_s": rate, "cold_requests": len(cold),
+            "cold_p50_ms": float(np.percentile(cold, 50)) if cold else None,
+            "cold_max_ms": max(cold) if cold else None,
+            "warm_p50_ms": float(np.percentile(warm, 50)) if warm else None,
+            "plan_build_ms_p50": float(np.percentile(builds, 50)) if builds else None,
+            "plan_build_ms_max": max(builds) if builds else None,
+            "all_converged": all(r["report"]["status"] == 0 for r in res),
+            "note": "plans built on first request while the serving launch runs on all teams but one"}
+
+
+def torch_empty(n):
+    import torch
+    return torch.empty(n, dtype=torch.float64, device="cuda")
 
 
 # ---------------------------------------------------------------------------

@@ -202,21 +202,23 @@ __device__ __forceinline__ int64_t fibre_start(const TcGridPass& g, int c) {
   return static_cast<int64_t>(p) * g.n * g.post + q;
 }
 
-// block = 64 fibres of one N tile x 4 groups of elements: thread (r, gq)
-// scans j = gq, gq + 4, ... of fibre r (consecutive threads read consecutive
-// fibres, so loads coalesce when the fibres are strided); the four partial
-// maxima meet in shared memory.
-__global__ void __launch_bounds__(256) tc_exp_kernel(const SplitArgs a) {
-  __shared__ unsigned long long smax[4][kTcN];
+// block = 64 fibres of one N tile x 16 groups of elements: thread (r, gq)
+// scans j = gq, gq + 16, ... of fibre r (consecutive threads read
+// consecutive fibres, so loads coalesce when the fibres are strided; 8 loads
+// in flight per thread); the 16 partial maxima meet in shared memory.
+constexpr int kTcExpGroups = 16;
+__global__ void __launch_bounds__(kTcN * kTcExpGroups) tc_exp_kernel(const SplitArgs a) {
+  __shared__ unsigned long long smax[kTcExpGroups][kTcN];
   const int gi = a.tasks[2 * blockIdx.x], nt = a.tasks[2 * blockIdx.x + 1];
   const TcGridPass g = a.gp[gi];
   const double* x = tc_src(g.in_sel, a.samples, a.y0, a.y1) + g.base;
-  const int r = threadIdx.x & (kTcN - 1), gq = threadIdx.x >> 6;
+  const int r = threadIdx.x % kTcN, gq = threadIdx.x / kTcN;
   const int c = nt * kTcN + r;
   unsigned long long mbits = 0;
   if (c < g.ncols) {
     const int64_t c0 = fibre_start(g, c);
-    for (int j = gq; j < g.n; j += 4) {
+#pragma unroll 8
+    for (int j = gq; j < g.n; j += kTcExpGroups) {
       const unsigned long long bits =
           static_cast<unsigned long long>(__double_as_longlong(ldcg(x + c0 + static_cast<int64_t>(j) * g.post))) &
           0x7FFFFFFFFFFFFFFFull;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(256) tc_exp_kernel(const SplitArgs a) {
   __syncthreads();
   if (gq == 0) {
 #pragma unroll
-    for (int q = 1; q < 4; ++q) mbits = smax[q][r] > mbits ? smax[q][r] : mbits;
+    for (int q = 1; q < kTcExpGroups; ++q) mbits = smax[q][r] > mbits ? smax[q][r] : mbits;
     int e = 0;
     if (mbits >= 0x7FF0000000000000ull) {
       e = kTcNonFinite;
@@ -340,45 +342,59 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
   const unsigned char* B = a.b + g.b_off + static_cast<int64_t>(nt) * ksteps * kTcBStep;
   const uint32_t sbase = smem_u32(sm);
 
-  int issued = 0;  // producer: stages whose copies were issued
-  if (threadIdx.x == 0) {
-    // producer: bulk copies of the A and B slices of every K step
+  // Warp-specialised roles, each run by a whole warp (the waits are
+  // warp-uniform, one elected lane issues): warp 0 streams the A and B slices
+  // of every K step into shared memory with bulk copies; warp 1 issues the
+  // tensor-core products; warps 2 and 3 wait for the accumulators.
+  int issued = 0;  // warp 0: stages whose copies were issued
+  if (warp == 0) {
     for (int s = 0; s < ksteps; ++s) {
       const int b = s % kTcStages;
-      if (s >= kTcStages && !mbar_wait(empty(b), ((s / kTcStages) - 1) & 1, a.timeout_ns)) {
-        atomicExch(&s_fail, 1);
-        break;
+      if (s >= kTcStages) {
+        const bool ok = mbar_wait(empty(b), ((s / kTcStages) - 1) & 1, a.timeout_ns);
+        if (!__all_sync(0xffffffffu, ok)) {
+          if (lane == 0) atomicExch(&s_fail, 1);
+          break;
+        }
       }
-      const uint32_t dst = sbase + static_cast<uint32_t>(b * kTcStageBytes);
-      mbar_expect_tx(full(b), kTcStageBytes);
-      bulk_g2s(dst, A + static_cast<int64_t>(s) * kTcAStep, kTcAStep, full(b));
-      bulk_g2s(dst + kTcAStep, B + static_cast<int64_t>(s) * kTcBStep, kTcBStep, full(b));
+      if (lane == 0) {
+        const uint32_t dst = sbase + static_cast<uint32_t>(b * kTcStageBytes);
+        mbar_expect_tx(full(b), kTcStageBytes);
+        bulk_g2s(dst, A + static_cast<int64_t>(s) * kTcAStep, kTcAStep, full(b));
+        bulk_g2s(dst + kTcAStep, B + static_cast<int64_t>(s) * kTcBStep, kTcBStep, full(b));
+      }
+      __syncwarp();
       ++issued;
     }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer: accumulator g (TMEM columns g*64 ..) gathers the products of
-    // digit slices s of C and t of X with s + t = g
+  } else if (warp == 1) {
+    // accumulator g (TMEM columns g*64 ..) gathers the products of digit
+    // slices s of C and t of X with s + t = g
     for (int s = 0; s < ksteps; ++s) {
       const int b = s % kTcStages;
-      if (!mbar_wait(full(b), (s / kTcStages) & 1, a.timeout_ns)) {
-        atomicExch(&s_fail, 1);
+      const bool ok = mbar_wait(full(b), (s / kTcStages) & 1, a.timeout_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicExch(&s_fail, 1);
         break;
       }
       tc_fence_after();
-      const uint32_t abase = sbase + static_cast<uint32_t>(b * kTcStageBytes);
-      const uint32_t bbase = abase + kTcAStep;
+      if (lane == 0) {
+        const uint32_t abase = sbase + static_cast<uint32_t>(b * kTcStageBytes);
+        const uint32_t bbase = abase + kTcAStep;
 #pragma unroll 1
-      for (int grp = 0; grp < kTcSlices; ++grp) {
+        for (int grp = 0; grp < kTcSlices; ++grp) {
 #pragma unroll 1
-        for (int sa = 0; sa <= grp; ++sa) {
-          const uint64_t da = smem_desc(abase + static_cast<uint32_t>(sa * kTcATile), 128, 256);
-          const uint64_t db = smem_desc(bbase + static_cast<uint32_t>((grp - sa) * kTcBTile), 128, 256);
-          tc_mma(tmem + static_cast<uint32_t>(grp * kTcN), da, db, (s > 0 || sa > 0) ? 1u : 0u);
+          for (int sa = 0; sa <= grp; ++sa) {
+            const uint64_t da = smem_desc(abase + static_cast<uint32_t>(sa * kTcATile), 128, 256);
+            const uint64_t db = smem_desc(bbase + static_cast<uint32_t>((grp - sa) * kTcBTile), 128, 256);
+            tc_mma(tmem + static_cast<uint32_t>(grp * kTcN), da, db, (s > 0 || sa > 0) ? 1u : 0u);
+          }
         }
+        tc_commit(empty(b));
       }
-      tc_commit(empty(b));
+      __syncwarp();
     }
-    tc_commit(done);  // every MMA issued above is complete when `done` flips
+    if (lane == 0) tc_commit(done);  // every MMA issued above is complete when `done` flips
+    __syncwarp();
   }
   // all threads: wait for the accumulators; the outcome is made uniform over
   // the block (the epilogue's TMEM loads need whole warps)
@@ -387,7 +403,7 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
   __syncthreads();
   const bool fail = ld_volatile_i32(&s_fail) != 0;
   if (fail) {
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // lane 0 of warp 0, which issued the copies
       atomicCAS(a.err, 0, static_cast<int>(FCT_ERR_TIMEOUT));
       // bounded wait for this CTA's copies still in flight: the last use of
       // every stage buffer
@@ -518,7 +534,7 @@ fct_status tc_run(const TcHost& T, const TcDevice& D, const TcWork& Wk, const do
     const int ng = T.gemm_off[p + 1] - T.gemm_off[p];
     if (ns > 0) {
       SplitArgs sa{D.gp, D.split_tasks + 2 * T.split_off[p], samples, y0, y1, Wk.b, Wk.f};
-      tc_exp_kernel<<<ns, 256, 0, st>>>(sa);
+      tc_exp_kernel<<<ns, kTcN * kTcExpGroups, 0, st>>>(sa);
       // chunks of 8 elements: 2 per K step, 4 per block row of the grid
       const unsigned gy = static_cast<unsigned>((2 * T.max_ksteps + 3) / 4);
       tc_digit_kernel<<<dim3(ns, gy), 256, 0, st>>>(sa);
