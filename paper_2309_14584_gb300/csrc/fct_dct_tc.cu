@@ -380,9 +380,9 @@ __global__ void __launch_bounds__(kTcGemmThreads, 1) tc_gemm_kernel(const GemmAr
       if (lane == 0) {
         const uint32_t abase = sbase + static_cast<uint32_t>(b * kTcStageBytes);
         const uint32_t bbase = abase + kTcAStep;
-#pragma unroll 1
+#pragma unroll
         for (int grp = 0; grp < kTcSlices; ++grp) {
-#pragma unroll 1
+#pragma unroll
           for (int sa = 0; sa <= grp; ++sa) {
             const uint64_t da = smem_desc(abase + static_cast<uint32_t>(sa * kTcATile), 128, 256);
             const uint64_t db = smem_desc(bbase + static_cast<uint32_t>((grp - sa) * kTcBTile), 128, 256);
