@@ -82,9 +82,8 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=SERVING_REQUESTS, help="requests per rate")
     ap.add_argument("--serving-kappa0", type=float, default=SERVING_KAPPA0,
                     help="Algorithm 2 bound on kappa(A) used to pick each serving shape's grid count")
-    ap.add_argument("--serving-team-blocks", type=int, default=38)
+    ap.add_argument("--serving-team-blocks", type=int, default=0, help="0 = chosen by measurement")
     ap.add_argument("--batch", type=int, default=BATCH, help="transforms per launch of the batched leg (0 = skip)")
-    ap.add_argument("--batch-team-blocks", type=int, default=16)
     ap.add_argument("--block-threads", type=int, default=0,
                     help="fix the launch shape (with --coef-lanes) instead of autotuning it")
     ap.add_argument("--coef-lanes", type=int, default=0)
@@ -812,8 +811,8 @@ def run_next_rows(F, w, opts, flush, steps=20) -> dict:
 
 def run_batched(args, F, w, opts, flush) -> dict:
     """B transforms of workload w (distinct Gaussian-cosine targets, one plan
-    and B - 1 clones) per launch of fct_execute_batch, teams of
-    args.batch_team_blocks blocks; L2 flushed between launches."""
+    and B - 1 clones) per launch of fct_execute_batch, the blocks per team
+    chosen by measurement; L2 flushed between launches."""
     import torch
     import workloads as W
     B = args.batch
@@ -826,18 +825,21 @@ def run_batched(args, F, w, opts, flush) -> dict:
         xs.append(x)
         cs.append(torch.empty(base.N, dtype=torch.float64, device="cuda"))
     hs = [p.handle for p in plans]
-    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks)
+    from paper_2309_14584_gb300.tune import autotune_team_blocks
+    tune = autotune_team_blocks(hs, xs, cs)   # outside the timed region
+    tb = tune["team_blocks"]
+    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=tb)
     alone = torch.empty(base.N, dtype=torch.float64, device="cuda")
     base.execute(xs[B - 1], alone)
     same = bool(torch.equal(alone, cs[B - 1]))
     for _ in range(args.warmup):
-        F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks, report=False)
-    ms = _timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks, report=False),
-                args.steps, flush)
+        F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False)
+    ms = _timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), args.steps, flush)
     for p in plans[1:]:
         p.close()
     base.close()
-    return {"workload": w.name, "transforms_per_launch": B, "team_blocks": args.batch_team_blocks, "path": "mixed",
+    return {"workload": w.name, "transforms_per_launch": B, "team_blocks": tb,
+            "team_blocks_tuning_ms": [[t, round(m, 3)] for t, m in tune["timings"]], "path": "mixed",
             "coeffs_per_launch": B * w.N, "ms_per_launch": statistics.mean(ms), "total_s": sum(ms) / 1e3, "ms": ms,
             "all_converged": all(r["status"] == 0 for r in reps),
             "max_iterations": max(r["iterations"] for r in reps),
@@ -876,22 +878,26 @@ def run_hetero_batch(args, F, opts) -> dict:
         xs.append(x)
         cs.append(torch.empty(p.N, dtype=torch.float64, device="cuda"))
     hs = [p.handle for p in plans]
-    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks)
+    from paper_2309_14584_gb300.tune import autotune_team_blocks
+    tune = autotune_team_blocks(hs, xs, cs, candidates=(8, 16, 32), reps=1)   # outside the timed region
+    tb = tune["team_blocks"]
+    reps = F.fct_execute_batch(hs, xs, cs, team_blocks=tb)
     order = sorted(range(len(plans)), key=lambda i: plans[i].N)
     small = order[0]
     alone = torch.empty(plans[small].N, dtype=torch.float64, device="cuda")
     plans[small].execute(xs[small], alone)
     same = bool(torch.equal(alone, cs[small]))
     checks = [(f"hetero:{ws[i].name}", ws[i], cs[i].cpu().numpy()) for i in order[:HETERO_CHECKED]]
-    ms = statistics.mean(_timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=args.batch_team_blocks,
-                                                            report=False), 2, torch.empty(1, device="cuda")))
+    ms = statistics.mean(_timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), 2,
+                                torch.empty(1, device="cuda")))
     sum_n = sum(p.N for p in plans)
     out = {"transforms_per_launch": len(plans), "value": sum_n / (ms / 1e3), "unit": UNIT, "ms_per_launch": ms,
            "coeffs_per_launch": sum_n, "samples_per_launch": sum(p.M for p in plans), "timed_launches": 2,
            "grid_selection_s": round(t_select, 1),
            "grid_count_over_3D_median": sorted(L / (3 * w.D) for L, w in zip(Ls, cands))[len(Ls) // 2],
            "all_converged": all(r["status"] == 0 for r in reps), "max_iterations": max(r["iterations"] for r in reps),
-           "batch_equals_alone": same, "team_blocks": args.batch_team_blocks, "path": "mixed",
+           "batch_equals_alone": same, "team_blocks": tb,
+           "team_blocks_tuning_ms": [[t, round(m, 1)] for t, m in tune["timings"]], "path": "mixed",
            "check_results": checks,
            "note": "inputs larger than L2; grid counts by Algorithm 2 (kappa0 = 20) before the timed region"}
     for p in plans:
@@ -942,7 +948,29 @@ def run_serving(args, F):
     t0 = time.perf_counter()
     shapes, sel = serving_workloads(args.serving_kappa0)
     t_select = time.perf_counter() - t0
-    eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=args.serving_team_blocks,
+    team_tuning = []
+    if args.serving_team_blocks <= 0:
+        # blocks per team by measurement: a burst of every shape twice, per candidate
+        for tb in (16, 38, 76):
+            e = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=2, team_blocks=tb,
+                              precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4, max_iter=20000)
+            xs = {}
+            for s, w in enumerate(shapes):
+                x = torch.empty(e.plans[s].M, dtype=torch.float64, device="cuda")
+                e.plans[s].sample(W.FAMILY_GAUSSCOS, W.gausscos_params(w.D * 1000, w.D), x)
+                xs[s] = x
+            burst = [(0.0, s, s) for s in range(len(shapes))] * 2
+            o = [torch.empty(e.plans[s].N, dtype=torch.float64, device="cuda") for _, s, _ in burst]
+            e.run(burst[:len(shapes)], xs, o[:len(shapes)])          # warm-up
+            t1 = time.perf_counter()
+            e.run(burst, xs, o)
+            team_tuning.append((tb, time.perf_counter() - t1))
+            e.close()
+            del xs, o
+        team_blocks = min(team_tuning, key=lambda t: t[1])[0]
+    else:
+        team_blocks = args.serving_team_blocks
+    eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=team_blocks,
                         precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4, max_iter=20000)
     inputs, truth = {}, {}
     for s, w in enumerate(shapes):
@@ -978,7 +1006,7 @@ def run_serving(args, F):
                 if key[1] != "poly" and shapes[s].N <= SERVING_CHECK_MAX_N:
                     served.setdefault(key, o.cpu().numpy())
     eng.close()
-    cold = run_serving_cold(args, F, shapes, inputs)
+    cold = run_serving_cold(args, F, shapes, inputs, team_blocks)
     checks = []
     for (s, v), c in sorted(served.items()):
         w = dataclasses.replace(shapes[s], params=W.gausscos_params(shapes[s].D * 1000 + v, shapes[s].D))
@@ -989,10 +1017,11 @@ def run_serving(args, F):
                       f"served Gaussian-cosine results of shapes with N <= {SERVING_CHECK_MAX_N} at the highest "
                       "rate are compared with the CPU oracle",
             "grid_selection_s": round(t_select, 2), "shapes": sel, "rates": out, "cold_plans": cold,
-            "team_blocks": args.serving_team_blocks, "check_results": checks}
+            "team_blocks": team_blocks, "team_blocks_tuning_s": [[t, round(x, 3)] for t, x in team_tuning],
+            "check_results": checks}
 
 
-def run_serving_cold(args, F, shapes, inputs, rate=25.0, n_req=60):
+def run_serving_cold(args, F, shapes, inputs, team_blocks, rate=25.0, n_req=60):
     """Plan-cache misses while serving: a fresh engine holds no plan; each
     shape's plan is built when its first request is admitted (grid counts as
     chosen by Algorithm 2 beforehand), while the serving launch runs on all
@@ -1002,8 +1031,8 @@ def run_serving_cold(args, F, shapes, inputs, rate=25.0, n_req=60):
     import numpy as np
     import workloads as W
     from paper_2309_14584_gb300.serving import ServingEngine
-    eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=args.serving_team_blocks,
-                        teams=max(1, 304 // args.serving_team_blocks - 1), lazy_plans=True, precision=F.FCT_MIXED,
+    eng = ServingEngine(shapes, hbm_budget_bytes=16e9, max_slots_per_shape=4, team_blocks=team_blocks,
+                        teams=max(1, 304 // team_blocks - 1), lazy_plans=True, precision=F.FCT_MIXED,
                         tol=1e-12, inner_tol=1e-4, max_iter=20000)
     raw = W.serving_requests(9, n_req, rate, len(shapes), poly_fraction=0.0)
     reqs = [(t, s, (s, ps % SERVING_VARIANTS)) for t, s, _, ps in raw]

@@ -1,11 +1,16 @@
-"""Launch-shape autotuner: time fct_execute for a few launch shapes of one
-plan on the caller's device-resident samples and keep the fastest.
+"""Autotuner: time a few launch configurations of one plan (or one batch) on
+the caller's device-resident inputs and keep the fastest.
 
-The shapes change only how the work is split over threads (block size,
-threads per coefficient in the A^T q gather, entries per lane in the A p
-gather); every shape solves the same system to the same tolerance, and the
-results differ only by the order of floating-point additions.  Timing uses
-CUDA events on the current stream; all arithmetic runs in libfct_gb300.so.
+Every candidate solves the same system to the same tolerance; the results
+differ only by the order of floating-point additions (or not at all: team
+sizes never change a transform's result).  Timing uses CUDA events on the
+current stream; all arithmetic runs in libfct_gb300.so.
+
+Dimensions:
+  * single transforms (autotune): block size, threads per coefficient in the
+    A^T q gather, entries per lane of the A p gather, and whether the grids
+    with long axes take their DCT passes on the tensor cores;
+  * batches and serving (autotune_team_blocks): blocks per team.
 """
 from __future__ import annotations
 
@@ -17,36 +22,72 @@ CANDIDATES = (
     dict(block_threads=512, coef_lanes=8),
     dict(block_threads=256, coef_lanes=8),
     dict(block_threads=128),
+    dict(block_threads=256, entries_per_lane=8),
+    dict(block_threads=512, entries_per_lane=8),
 )
+TEAM_BLOCKS = (8, 16, 19, 38, 76)
+
+
+def _time(fn, reps: int) -> float:
+    import torch
+    fn()
+    for _ in range(2):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
 
 
 def autotune(support, sizes, nodes, samples, options: dict, candidates=CANDIDATES, reps: int = 10) -> dict:
     """Returns {"options": fastest options (options updated with a candidate),
     "ms": its mean time, "timings": [(candidate, ms) for each candidate that
-    converged]}.  samples: device double[M] of this L-grid."""
+    converged]}.  samples: device double[M] of this L-grid.  When the plan has
+    grids whose DCT runs on the tensor cores, every candidate is also timed
+    with those passes on the FP64 units (tensor_dct = -1)."""
     import torch
 
+    cands = [dict(c) for c in candidates]
+    probe = F.Plan(support, sizes, nodes, **options)
+    has_tc = probe.info.get("tensor_dct_grids", 0) > 0
+    probe.close()
+    if has_tc and "tensor_dct" not in options:
+        cands += [dict(c, tensor_dct=-1) for c in candidates]
     timings = []
-    for cand in candidates:
+    for cand in cands:
         opts = dict(options, **cand)
         plan = F.Plan(support, sizes, nodes, **opts)
         try:
             c = torch.empty(plan.N, dtype=torch.float64, device=samples.device)
             if plan.execute(samples, c)["status"] != 0:
                 continue
-            for _ in range(2):
-                plan.execute(samples, c, report=False)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record()
-            for _ in range(reps):
-                plan.execute(samples, c, report=False)
-            e1.record()
-            torch.cuda.synchronize()
-            timings.append((cand, e0.elapsed_time(e1) / reps))
+            timings.append((cand, _time(lambda: plan.execute(samples, c, report=False), reps)))
         finally:
             plan.close()
     if not timings:
         raise RuntimeError("no launch shape converged")
     cand, ms = min(timings, key=lambda t: t[1])
     return {"options": dict(options, **cand), "ms": ms, "timings": timings}
+
+
+def autotune_team_blocks(handles, samples, coeffs, candidates=TEAM_BLOCKS, reps: int = 3) -> dict:
+    """Blocks per team for one batch (fct_execute_batch of the given plan
+    handles and device buffers): {"team_blocks": fastest, "ms": its time per
+    launch, "timings": [(team_blocks, ms)]}.  Candidates larger than the
+    batch can use are skipped by the library's own clamp, so the times of
+    those candidates repeat."""
+    timings = []
+    for tb in candidates:
+        reps_ = F.fct_execute_batch(handles, samples, coeffs, team_blocks=tb)
+        if not all(r["status"] == 0 for r in reps_):
+            continue
+        ms = _time(lambda: F.fct_execute_batch(handles, samples, coeffs, team_blocks=tb, report=False), reps)
+        timings.append((tb, ms))
+    if not timings:
+        raise RuntimeError("no team size converged")
+    tb, ms = min(timings, key=lambda t: t[1])
+    return {"team_blocks": tb, "ms": ms, "timings": timings}

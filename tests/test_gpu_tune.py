@@ -43,3 +43,32 @@ def test_team_barrier_probe_rejects_bad_arguments():
         F.fct_measure_team_barrier(100000, 256, 10)
     with pytest.raises(F.FctError):
         F.fct_measure_team_barrier(4, 96, 10)
+
+
+def test_team_size_autotune_keeps_batch_results_bit_identical():
+    """The team-size tuner picks one of its candidates; every team size gives
+    the same coefficients bit for bit (reductions follow a fixed order that
+    does not depend on the team), equal to each transform alone."""
+    from paper_2309_14584_gb300.tune import TEAM_BLOCKS, autotune_team_blocks
+    ws = [W.make_workload(f"b{i}", 60 + i, 3, 8, 9, 1, 9, W.FAMILY_GAUSSCOS) for i in range(6)]
+    plans = [F.Plan(w.support, w.sizes, w.nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4) for w in ws]
+    xs, cs = [], []
+    for p, w in zip(plans, ws):
+        x = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(w.family, w.params, x)
+        xs.append(x)
+        cs.append(torch.empty(p.N, dtype=torch.float64, device="cuda"))
+    hs = [p.handle for p in plans]
+    r = autotune_team_blocks(hs, xs, cs, reps=1)
+    assert r["team_blocks"] in TEAM_BLOCKS and len(r["timings"]) == len(TEAM_BLOCKS)
+    F.fct_execute_batch(hs, xs, cs, team_blocks=r["team_blocks"])
+    tuned = [c.clone() for c in cs]
+    F.fct_execute_batch(hs, xs, cs, team_blocks=8)
+    for a, b in zip(tuned, cs):
+        assert torch.equal(a, b)
+    for p, x, a in zip(plans, xs, tuned):
+        alone = torch.empty_like(a)
+        assert p.execute(x, alone)["status"] == 0
+        assert torch.equal(alone, a)
+    for p in plans:
+        p.close()
