@@ -342,6 +342,19 @@ def algorithmic_bytes(info, rep, precision):
     return dct + rep["iterations"] * it32 + rep["refinements"] * it64
 
 
+def gather_roofline(info, rep, launch_s, peak_gloads):
+    """Scattered loads per launch: every CG iteration and every refinement
+    sweep gathers one vector element per table entry in each of its two
+    alias passes (A p bin-major, A^T q coefficient-major): 2 K N per pass
+    pair; against the random-gather rate measured by fct_measure_l2."""
+    K, N = info["K"], info["N"]
+    loads = 2.0 * K * N * (rep["iterations"] + rep["refinements"])
+    achieved = loads / launch_s / 1e9
+    return {"bound": "l1_gather", "achieved": achieved, "peak": peak_gloads, "unit": "Gloads/s",
+            "frac": achieved / peak_gloads, "loads_per_launch": loads,
+            "peak_kind": "random 8-byte loads of an L2-resident buffer, measured live by fct_measure_l2"}
+
+
 def profiled_traffic(profile_name: str):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     kernel source changed since that capture."""
@@ -620,6 +633,9 @@ def run_gpu(args):
                           "rel_err_vs_oracle": r["rel_err"], "deterministic": r["deterministic"],
                           "e2e_value": w.N / r["e2e_s"], "meets_1e-10": p in valid}
                       for p, r in results.items()},
+        # the binding roof of the CG loop: scattered 4-8 byte loads (one per table
+        # entry per alias pass) against the measured random-gather rate
+        "gather_roofline": gather_roofline(info, R0["rep"], mean_launch_s, roofs["l2"]["gather_gloads_per_s"]),
         "roofs_measured": {"l2_read_gbs": l2, "l2_gather_sector_gbs": roofs["l2"]["gather_sector_gbs"],
                            "l2_gather_gloads_per_s": roofs["l2"]["gather_gloads_per_s"],
                            "fp64_tflops": roofs["fp64_tflops"]},
