@@ -20,8 +20,9 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfct_gb300.so")
 
-SOURCES = ["fct_solve_k256.cu", "fct_solve_k128.cu", "fct_solve_k512.cu", "fct_device.cu", "fct_plan_device.cu",
-           "fct_plan_host.cpp", "fct_peaks.cu", "fct_dct_tc.cu"]
+SOURCES = ["fct_solve_k256.cu", "fct_solve_k128.cu", "fct_solve_k512.cu", "fct_solve_k256d.cu", "fct_solve_k128d.cu",
+           "fct_solve_k512d.cu", "fct_device.cu", "fct_plan_device.cu", "fct_plan_host.cpp", "fct_peaks.cu",
+           "fct_dct_tc.cu"]
 HEADERS = ["fct_internal.h", "fct_common.cuh", "fct_solver.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

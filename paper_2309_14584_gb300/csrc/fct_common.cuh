@@ -360,5 +360,8 @@ __device__ __forceinline__ void st_release_sys_i32(int* p, int v) {
 
 // The team solver kernel (defined in fct_solver.cuh, instantiated per block
 // size in fct_solve_k128.cu, fct_solve_k256.cu and fct_solve_k512.cu).
-template <int BT, bool SV>
+// DEEP = 1: the gathers stage twice as many entries per lane and round (8
+// per row lane, 16 per coefficient lane), for plans with long rows or many
+// grids, whose gathers stream their tables from DRAM.
+template <int BT, bool SV, int DEEP>
 __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs a);

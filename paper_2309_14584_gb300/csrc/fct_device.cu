@@ -284,6 +284,7 @@ struct fct_plan_s {
   std::vector<int32_t> ru_first, rowptr_h;  // for the shared-memory sizing of other team sizes
   std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
   bool stage_values = false;                // single launches stage the CG loop's entry values too
+  int kernel_kind = 0;                      // solver kernel variant of single launches (kKernel*)
   double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
   // DCT passes on the tensor cores (grids with a long axis; null when none):
@@ -308,25 +309,31 @@ fct_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
+// Variants of the team solver kernel: plain; kKernelStaged also stages the
+// CG loop's entry values in shared memory (single transforms whose tables
+// fit); kKernelDeep stages twice as many gather entries per lane and round
+// (single transforms of plans with wide rows or many grids, whose tables
+// stream from DRAM).  See choose_shape.
+enum { kKernelPlain = 0, kKernelStaged = 1, kKernelDeep = 2 };
+
 template <int BT>
-const void* kernel_ptr(bool stage_values) {
-  return stage_values ? reinterpret_cast<const void*>(&fct_solve_kernel<BT, true>)
-                      : reinterpret_cast<const void*>(&fct_solve_kernel<BT, false>);
+const void* kernel_ptr(int kind) {
+  if (kind == kKernelStaged) return reinterpret_cast<const void*>(&fct_solve_kernel<BT, true, 0>);
+  if (kind == kKernelDeep) return reinterpret_cast<const void*>(&fct_solve_kernel<BT, false, 1>);
+  return reinterpret_cast<const void*>(&fct_solve_kernel<BT, false, 0>);
 }
 
-// stage_values: the variant that also stages the CG loop's entry values in
-// shared memory (single transforms whose tables fit; see choose_shape).
-const void* solve_kernel_for(int bt, bool stage_values = false) {
+const void* solve_kernel_for(int bt, int kind = kKernelPlain) {
   switch (bt) {
-    case 128: return kernel_ptr<128>(stage_values);
-    case 512: return kernel_ptr<512>(stage_values);
-    default: return kernel_ptr<256>(stage_values);
+    case 128: return kernel_ptr<128>(kind);
+    case 512: return kernel_ptr<512>(kind);
+    default: return kernel_ptr<256>(kind);
   }
 }
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_t st, bool stage_values = false) {
+fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_t st, int kind = kKernelPlain) {
   // Reset the per-launch header (queue head, error flag); team barriers are
   // self-cleaning and re-zeroed only after an abandoned launch.
   // Single-transform launches need no reset (team counters reset themselves at
@@ -339,7 +346,7 @@ fct_status launch_solve(fct_plan P, const SolveArgs& args, int grid, cudaStream_
   }
   P->dirty_state = false;
   void* kargs[] = {const_cast<SolveArgs*>(&args)};
-  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads, stage_values), dim3(grid),
+  FCT_CUDA(cudaLaunchCooperativeKernel(solve_kernel_for(P->block_threads, kind), dim3(grid),
                                        dim3(P->block_threads), kargs,
                                        static_cast<size_t>(args.smem_bytes), st));
   return FCT_OK;
@@ -399,8 +406,10 @@ fct_status choose_shape(fct_plan P) {
   cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
   cap = std::max(cap, 0) & ~15;
   FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, true), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                cap));
+  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, kKernelStaged),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, kKernelDeep),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   P->blocks_per_sm = per_sm;
   P->smem_cap = cap;
   P->max_coresident = per_sm * prop.multiProcessorCount;
@@ -420,9 +429,15 @@ fct_status choose_shape(fct_plan P) {
   FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, kfn, P->block_threads, P->smem_bytes));
   if (chk * prop.multiProcessorCount < P->grid_blocks) return fail(FCT_ERR_CUDA, "solver grid does not fit");
   if (P->stage_values) {
-    FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, solve_kernel_for(P->block_threads, true),
+    FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, solve_kernel_for(P->block_threads, kKernelStaged),
                                                            P->block_threads, P->smem_bytes));
     if (chk * prop.multiProcessorCount < P->grid_blocks) P->stage_values = false;
+  }
+  P->kernel_kind = P->stage_values ? kKernelStaged : kKernelPlain;
+  if (!P->stage_values && (P->hp.n_wide_units > 0 || P->K >= 64)) {
+    FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&chk, solve_kernel_for(P->block_threads, kKernelDeep),
+                                                           P->block_threads, P->smem_bytes));
+    if (chk * prop.multiProcessorCount >= P->grid_blocks) P->kernel_kind = kKernelDeep;
   }
   return FCT_OK;
 }
@@ -996,7 +1011,7 @@ fct_status fct_execute(fct_plan P, const double* samples, double* coeffs, void* 
   a.smem_bytes = P->smem_bytes;
   fct_status s = run_tc_passes(P, samples, st, &a.single);
   if (s != FCT_OK) return s;
-  s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
+  s = launch_solve(P, a, P->grid_blocks, st, P->kernel_kind);
   if (s != FCT_OK) return s;
   if (rep) return read_report(P, P->drep, st, rep);
   return FCT_OK;
@@ -1034,7 +1049,7 @@ fct_status fct_plan_rhs(fct_plan P, const double* samples, double* b, int64_t* b
   a.smem_bytes = P->smem_bytes;
   fct_status s = run_tc_passes(P, samples, st, &a.single);
   if (s != FCT_OK) return s;
-  s = launch_solve(P, a, P->grid_blocks, st, P->stage_values);
+  s = launch_solve(P, a, P->grid_blocks, st, P->kernel_kind);
   if (s != FCT_OK) return s;
   FCT_CUDA(cudaMemcpyAsync(b, P->hp.b, sizeof(double) * P->R, cudaMemcpyDeviceToDevice, st));
   FCT_CUDA(cudaStreamSynchronize(st));
@@ -1178,6 +1193,7 @@ fct_status fct_plan_clone(fct_plan* out, fct_plan src) {
   C->blocks_per_sm = src->blocks_per_sm;
   C->smem_bytes = src->smem_bytes;
   C->stage_values = src->stage_values;
+  C->kernel_kind = src->kernel_kind;
   C->smem_cap = src->smem_cap;
   C->ru_first = src->ru_first;
   C->rowptr_h = src->rowptr_h;

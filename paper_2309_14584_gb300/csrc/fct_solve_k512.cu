@@ -3,5 +3,5 @@
 // kernels build in parallel.
 #include "fct_solver.cuh"
 
-template __global__ void fct_solve_kernel<512, false>(const SolveArgs a);
-template __global__ void fct_solve_kernel<512, true>(const SolveArgs a);
+template __global__ void fct_solve_kernel<512, false, 0>(const SolveArgs a);
+template __global__ void fct_solve_kernel<512, true, 0>(const SolveArgs a);

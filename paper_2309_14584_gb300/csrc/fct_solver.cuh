@@ -238,8 +238,9 @@ __device__ __forceinline__ RowUnit row_unit_geom(const DevPlan& P, const BlockTa
 }
 
 // Row gather: for each value functor, sum over the row's entries of
-// w_j * val(col_j).  Entries are staged four per lane at a time.
-template <typename V, typename WT, int NV, bool SV, typename Val1, typename Val2>
+// w_j * val(col_j).  Entries are staged EPR per lane at a time (4, or 8 in the
+// deep kernel variant for plans with long rows).
+template <typename V, typename WT, int NV, bool SV, int EPR, typename Val1, typename Val2>
 __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
                                             int k, int wk, int* row_out, bool* lead, Val1 val1, Val2 val2, V* out1,
                                             V* out2) {
@@ -261,23 +262,23 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += 4 * gl) {
-      int c[4];
-      WT wv[4];
+    for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+      int c[EPR];
+      WT wv[EPR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < EPR; ++i) {
         const int j = j0 + i * gl;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
         wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
-      V v1[4], v2[4];
+      V v1[EPR], v2[EPR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < EPR; ++i) {
         v1[i] = c[i] >= 0 ? val1(c[i]) : V(0);
         if (NV > 1) v2[i] = c[i] >= 0 ? val2(c[i]) : V(0);
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < EPR; ++i)
         if (c[i] >= 0) {
           a1 = fma(static_cast<V>(wv[i]), v1[i], a1);
           if (NV > 1) a2 = fma(static_cast<V>(wv[i]), v2[i], a2);
@@ -290,17 +291,17 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
   *lead = (row < g.r1) && (lane & (wide ? 31 : g.lc - 1)) == 0;
 }
 
-template <typename V, typename WT, bool SV, typename Val>
+template <typename V, typename WT, bool SV, int EPR, typename Val>
 __device__ __forceinline__ V row_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u, int k,
                                         int wk, int* row_out, bool* lead, Val val) {
   V a, b;
-  row_gather_n<V, WT, 1, SV>(P, T, w, u, k, wk, row_out, lead, val, val, &a, &b);
+  row_gather_n<V, WT, 1, SV, EPR>(P, T, w, u, k, wk, row_out, lead, val, val, &a, &b);
   return a;
 }
 
 // Phase-A gather of the interleaved {s, p}: as = sum w s[col], ap = sum w p[col]
 // (ap skipped on the first iteration, when p is not defined yet).
-template <typename V, typename V2, typename WT, bool SV>
+template <typename V, typename V2, typename WT, bool SV, int EPR>
 __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int u,
                                              int k, int wk, int* row_out, bool* lead, const V2* sp, bool first, V* as,
                                              V* ap) {
@@ -320,25 +321,25 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += 4 * gl) {
-      int c[4];
-      WT wv[4];
+    for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+      int c[EPR];
+      WT wv[EPR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < EPR; ++i) {
         const int j = j0 + i * gl;
         c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
         wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
       }
-      V2 v[4];
+      V2 v[EPR];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < EPR; ++i) {
         // plain (L1-cached) loads: {s, p} is written only in the phase before
         // the last team barrier, whose acquire drops this SM's stale L1 lines
         if (c[i] >= 0) v[i] = sp[c[i]];
         else { v[i].x = V(0); v[i].y = V(0); }
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < EPR; ++i)
         if (c[i] >= 0) {
           a1 = fma(static_cast<V>(wv[i]), v[i].x, a1);
           if (!first) a2 = fma(static_cast<V>(wv[i]), v[i].y, a2);
@@ -381,7 +382,7 @@ __device__ __forceinline__ void wide_row_combine(int wk, V* a, V* b, bool* lead)
 // Coefficient gather: acc = sum over grids l (this lane's share, l = lane,
 // lane + L, ...) of w[l][m] * val(crow[l][m]); up to 8 entries per lane are
 // staged together.
-template <typename V, typename WT, bool SV, typename Val>
+template <typename V, typename WT, bool SV, int EPC, typename Val>
 __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int c, int k,
                                          int wk, int* m_out, bool* lead, Val val) {
   const int L = P.coef_lanes;
@@ -396,20 +397,20 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
   V acc = V(0);
   if (m < P.N) {
     const int64_t N = P.N;
-    for (int lb = lane; lb < P.K; lb += 8 * L) {
-      int idx[8];
-      WT wv[8];
+    for (int lb = lane; lb < P.K; lb += EPC * L) {
+      int idx[EPC];
+      WT wv[EPC];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
+      for (int i = 0; i < EPC; ++i) {
         const int l = lb + i * L;
         idx[i] = l < P.K ? (cr ? cr[l * cpc + mi] : __ldg(P.crow + l * N + m)) : -1;
         wv[i] = l < P.K ? (wsm ? wsm[l * cpc + mi] : __ldg(w + l * N + m)) : WT(0);
       }
-      V v[8];
+      V v[EPC];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = idx[i] >= 0 ? val(idx[i]) : V(0);
+      for (int i = 0; i < EPC; ++i) v[i] = idx[i] >= 0 ? val(idx[i]) : V(0);
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < EPC; ++i)
         if (idx[i] >= 0) acc = fma(static_cast<V>(wv[i]), v[i], acc);
     }
   }
@@ -450,7 +451,7 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
 constexpr int kUnitGroup = 16;  // units per flush of the per-warp partials
 
 
-template <int BT, typename V, typename WT, typename XT, bool SV>
+template <int BT, typename V, typename WT, typename XT, bool SV, int DEEP>
 __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const WT* wcsr, const WT* wcm,
                           typename Vec2<V>::T* sp, V* q, XT* x, double gamma0, double tol, int max_iter, int stall,
                           int* iters_out, double* gamma_out, int* status_out, double* red) {
@@ -508,7 +509,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     // ================= phase A: q = A s + beta A p
     {
       auto gather_a = [&](int u, int k, V* as, V* ap, int* row, bool* lead) {
-        row_gather_sp<V, V2, WT, SV>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
+        row_gather_sp<V, V2, WT, SV, (4 << DEEP)>(P, T, wcsr, u, k, wk, row, lead, sp, first, as, ap);
       };
       int u = tm.rank;
       V as = V(0), ap = V(0);
@@ -587,7 +588,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       if (wk >= 0) {
         if (c < ncc) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT, SV>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
+          t = coef_gather<V, WT, SV, (8 << DEEP)>(P, T, wcm, c, 0, wk, &m, &lead, [&](int i) { return q[i]; });
         }
       } else {
         const double dl = widen(warp0_sum(part_r, nru));
@@ -612,7 +613,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
       for (; c < ncc; c += tm.G, ++k) {
         if (k > 0 && wk >= 0) {
           own_load(c, &o, &xo);
-          t = coef_gather<V, WT, SV>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
+          t = coef_gather<V, WT, SV, (8 << DEEP)>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
         PT part = pzero_part(PT{});
         if (wk >= 0 && lead) {
@@ -902,7 +903,7 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
 // nonempty bins, then the FP64 solve, or FP64 normal-residual sweeps around
 // FP32 inner solves (mixed).
 // ---------------------------------------------------------------------------
-template <int BT, bool SV>
+template <int BT, bool SV, int DEEP>
 __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned char* dsm, int smem_bytes) {
   const DevPlan& P = *J.plan;
   BlockTabs T;
@@ -954,7 +955,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       int m = 0;
       bool lead = false;
       double t = 0.0;
-      if (wk >= 0) t = coef_gather<double, double, SV>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
+      if (wk >= 0) t = coef_gather<double, double, SV, (8 << DEEP)>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
       double part = 0.0;
       if (lead) {
         stcg(P.sp + m, make_double2(t, 0.0));
@@ -973,7 +974,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
   if (!isfinite(gamma0)) {
     status = FCT_ERR_NONFINITE;
   } else if (J.precision != FCT_MIXED) {
-    if (!cg_normal<BT, double, double, double, SV>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, J.coeffs, gamma0, J.tol,
+    if (!cg_normal<BT, double, double, double, SV, DEEP>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, J.coeffs, gamma0, J.tol,
                                                J.max_iter, 0, &iters, &gfinal, &status, red))
       return false;
   } else if (gamma0 > 0.0) {
@@ -998,7 +999,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       if (P.n_w_units > 0) {
         if (!pcg_normal_w<BT>(P, tm, T, g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in, &st_in))
           return false;
-      } else if (!cg_normal<BT, float, float, float, SV>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32,
+      } else if (!cg_normal<BT, float, float, float, SV, DEEP>(P, tm, T, P.wcsr32, P.wcm32, P.sp32, P.q32, P.dx32,
                                                      g64 * ci * ci, J.inner_tol, J.max_iter, 64, &it_in, &g_in,
                                                      &st_in, red)) {
         return false;
@@ -1020,7 +1021,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         bool lead = false;
         double ax = 0.0, unused = 0.0;
         if (wk >= 0)
-          ax = row_gather<double, double, SV>(P, T, P.wcsr, u, ku, wk, &row, &lead,
+          ax = row_gather<double, double, SV, (4 << DEEP)>(P, T, P.wcsr, u, ku, wk, &row, &lead,
                                               [&](int m) { return ldcg(x + m); });
         if (u < nwide) wide_row_combine<BT / 32 - 1>(wk, &ax, &unused, &lead);
         if (lead) stcg(P.rres + row, ldcg(P.b + row) - ax);
@@ -1032,7 +1033,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         bool lead = false;
         double t = 0.0;
         if (wk >= 0)
-          t = coef_gather<double, double, SV>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
+          t = coef_gather<double, double, SV, (8 << DEEP)>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
         double part = 0.0;
         if (lead) {
           stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));
@@ -1059,7 +1060,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         int it64 = 0, st64 = FCT_OK;
         double g_out = g64;
         const double tol_eff = J.tol * sqrt(gamma0 / g64);
-        if (!cg_normal<BT, double, double, double, SV>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, x, g64, tol_eff, J.max_iter,
+        if (!cg_normal<BT, double, double, double, SV, DEEP>(P, tm, T, P.wcsr, P.wcm, P.sp, P.q, x, g64, tol_eff, J.max_iter,
                                                    0, &it64, &g_out, &st64, red))
           return false;
         iters += it64;
@@ -1082,7 +1083,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
   return true;
 }
 
-template <int BT, bool SV>
+template <int BT, bool SV, int DEEP>
 __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs a) {
   __shared__ double red[BT / 32 + 2];
   __shared__ int s_job;
@@ -1140,7 +1141,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
       const SolveJob J = s_jobdesc;
       __syncthreads();
       if (j < 0) break;
-      if (!solve_job<BT, SV>(J, tm, red, dsm, a.smem_bytes)) {
+      if (!solve_job<BT, SV, DEEP>(J, tm, red, dsm, a.smem_bytes)) {
         // Abandoned (a bounded wait expired in this team or another one): the
         // job is reported finished with the launch's error code, the error is
         // published in the ring for the host, the job no longer counts as
@@ -1176,7 +1177,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
     return;
   }
   if (a.jobs == nullptr) {
-    if (team == 0 && solve_job<BT, SV>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
+    if (team == 0 && solve_job<BT, SV, DEEP>(a.single, tm, red, dsm, a.smem_bytes)) team_exit(tm);
     return;
   }
   for (;;) {
@@ -1187,7 +1188,7 @@ __global__ void __launch_bounds__(BT, 512 / BT) fct_solve_kernel(const SolveArgs
     const int j = s_job;
     __syncthreads();
     if (j >= a.njobs) break;
-    if (!solve_job<BT, SV>(a.jobs[j], tm, red, dsm, a.smem_bytes)) return;
+    if (!solve_job<BT, SV, DEEP>(a.jobs[j], tm, red, dsm, a.smem_bytes)) return;
   }
   team_exit(tm);
 }
