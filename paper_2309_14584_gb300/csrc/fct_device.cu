@@ -397,6 +397,11 @@ fct_status choose_shape(fct_plan P) {
   const void* kfn = solve_kernel_for(P->block_threads);
   cudaFuncAttributes fa;
   FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
+  for (int kind : {kKernelStaged, kKernelDeep}) {  // the largest static shared memory of the variants
+    cudaFuncAttributes fk;
+    FCT_CUDA(cudaFuncGetAttributes(&fk, solve_kernel_for(P->block_threads, kind)));
+    fa.sharedSizeBytes = std::max(fa.sharedSizeBytes, fk.sharedSizeBytes);
+  }
   int per_sm = 0;
   FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->block_threads, 0));
   if (per_sm < 1) return fail(FCT_ERR_CUDA, "solver kernel cannot be resident");
