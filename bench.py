@@ -61,11 +61,11 @@ PATH_OPTIONS = {   # precision: 0 = FCT_FP64, 1 = FCT_MIXED (include/fct.h)
 
 # cases of --profile: (workload factory name, path options, plan options)
 PROFILE_CASES = {
-    "d10_mixed": ("config_d10_rational", "mixed", {}),
-    "d10_fp64": ("config_d10_rational", "fp64", {}),
+    "d10_mixed": ("config_d10_rational", "mixed", {"block_threads": 512}),
+    "d10_fp64": ("config_d10_rational", "fp64", {"block_threads": 256}),
     "d6_mixed": ("config_d6_gausscos", "mixed", {}),
     "d2_tensor_dct": ("tc_profile_workload", "mixed", {}),
-    "sparse_d100": ("sparse_profile_workload", "mixed", {}),
+    "sparse_d100": ("sparse_profile_workload", "mixed", {"block_threads": 512}),
 }
 
 
@@ -1162,6 +1162,9 @@ def run_profile(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile": args.profile, "workload": w.name, "N": plan.N, "M": plan.M,
                       "R": plan.info["R"], "K": plan.info["K"], "tensor_dct_grids": plan.info["tensor_dct_grids"],
+                      "row_units": plan.info["row_units"], "wide_rows": plan.info["wide_rows"],
+                      "coef_chunks": plan.info["coef_chunks"], "coef_split": plan.info["coef_split"],
+                      "block_threads": plan.info["block_threads"], "grid_blocks": plan.info["grid_blocks"],
                       "report": rep}))
     plan.close()
 

@@ -124,6 +124,15 @@ typedef struct {
                          fct_execute, fct_execute_host and fct_plan_rhs; batches,
                          serving and fct_execute_noalloc transform every grid on
                          the FP64 units.                                              */
+  int coef_split;     /* A^T q gather layout: 0 = auto (on for plans of 64 or more grids),
+                         1 = grid-split: each gather warp takes 32 consecutive
+                         coefficients of a chunk and every (block warps - 1)-th grid,
+                         so its loads of the coefficient-major tables are coalesced and
+                         its q reads fall in one grid's rows; the warps' partial sums
+                         are added in warp order (coef_lanes is then unused).
+                         -1 = lane-split: coef_lanes threads of one warp per
+                         coefficient.  Both give results independent of the team
+                         size; they differ from each other by rounding order only. */
 } fct_options;
 
 #define FCT_PLAN_BUILD_AUTO 0
@@ -152,6 +161,10 @@ typedef struct {
   int64_t device_bytes;     /* tables + workspace held on the device               */
   int64_t normal_nnz;       /* nonzeros of W = A^T A when the plan stores it, else 0 */
   int64_t tensor_dct_grids; /* grids whose DCT runs on the tensor cores (fct_execute) */
+  int32_t coef_split;       /* 1 when the A^T q gather is grid-split (fct_options.coef_split) */
+  int32_t row_units;        /* A p gather units of the solver (each adds one partial sum) */
+  int32_t wide_rows;        /* rows gathered by a whole block (the first row units)     */
+  int32_t coef_chunks;      /* A^T q gather units of the solver                         */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,

@@ -375,7 +375,8 @@ size_t block_smem_need(const fct_plan P, int G, int rank, bool with_values) {
       ints += (r1 - r0 + 1) + 2 * static_cast<size_t>(P->w_rowptr_h[r1] - P->w_rowptr_h[r0]);
     }
   ints += 5 * nA + nB + 2 * nW + 1;
-  return static_cast<size_t>(hp.mats_smem) * sizeof(double) + 4 * ints;
+  const size_t cmb = hp.coef_split ? coef_combine_bytes(P->block_threads) : 0;
+  return cmb + static_cast<size_t>(hp.mats_smem) * sizeof(double) + 4 * ints;
 }
 
 size_t team_smem_need(const fct_plan P, int G, bool with_values) {
@@ -410,6 +411,8 @@ fct_status choose_shape(fct_plan P) {
   int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / per_sm) - reserve - static_cast<int>(fa.sharedSizeBytes);
   cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
   cap = std::max(cap, 0) & ~15;
+  if (P->hp.coef_split && cap < coef_combine_bytes(P->block_threads))
+    return fail(FCT_ERR_CUDA, "no shared memory for the grid-split gather");
   FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, kKernelStaged),
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
@@ -498,6 +501,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
     return fail(FCT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
   if (o.coef_lanes != 0 && (o.coef_lanes < 1 || o.coef_lanes > 16 || (o.coef_lanes & (o.coef_lanes - 1))))
     return fail(FCT_ERR_INVALID_ARG, "coef_lanes must be 0 or a power of two <= 16");
+  if (o.coef_split < -1 || o.coef_split > 1) return fail(FCT_ERR_INVALID_ARG, "coef_split must be -1, 0 or 1");
   if (o.entries_per_lane != 0 && o.entries_per_lane != 2 && o.entries_per_lane != 4 && o.entries_per_lane != 8)
     return fail(FCT_ERR_INVALID_ARG, "entries_per_lane must be 0, 2, 4 or 8");
   int ndev = 0;
@@ -594,9 +598,14 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.D = D;
   hp.M = H.M;
   hp.npass = H.npass;
-  hp.coef_lanes = L;
+  // grid-split A^T q gather: coalesced reads of the coefficient-major tables
+  // (32 consecutive coefficients per warp load), and a warp's q reads fall in
+  // one grid's rows; pays where each coefficient has many grids
+  const bool split = o.coef_split > 0 || (o.coef_split == 0 && K >= kCoefSplitMinGrids);
+  hp.coef_split = split ? 1 : 0;
+  hp.coef_lanes = split ? 1 : L;
   hp.workers = workers;
-  hp.coefs_per_chunk = workers / L;
+  hp.coefs_per_chunk = split ? 32 : workers / L;
   hp.n_coef_chunks = static_cast<int32_t>((N + hp.coefs_per_chunk - 1) / hp.coefs_per_chunk);
   hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
   std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
@@ -884,6 +893,10 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->coef_lanes = P->hp.coef_lanes;
   info->device_bytes = static_cast<int64_t>(P->dbytes);
   info->normal_nnz = P->hp.n_w_units > 0 ? static_cast<int64_t>(P->w_rowptr_h.back()) : 0;
+  info->coef_split = P->hp.coef_split;
+  info->row_units = P->hp.n_row_units;
+  info->wide_rows = P->hp.n_wide_units;
+  info->coef_chunks = P->hp.n_coef_chunks;
   info->tensor_dct_grids = 0;
   if (P->tc)
     for (char g : P->tc->grid_tc) info->tensor_dct_grids += g ? 1 : 0;

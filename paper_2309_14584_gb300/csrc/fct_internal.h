@@ -111,6 +111,16 @@ struct TcHost {
   bool empty() const { return npass == 0; }
 };
 
+// Plans with at least this many grids take the grid-split A^T q gather
+// unless fct_options.coef_split says otherwise.
+constexpr int kCoefSplitMinGrids = 64;
+// Shared memory of the grid-split gather's partial sums, at the start of a
+// block's dynamic shared memory: two buffers of (gather warps x 32) doubles.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int coef_combine_bytes(int block_threads) { return 2 * (block_threads / 32 - 1) * 32 * 8; }
+
 // Everything the solver kernel needs about one plan; lives in device memory.
 struct DevPlan {
   int32_t N, R, K, D;
@@ -121,6 +131,7 @@ struct DevPlan {
   int32_t n_coef_chunks;     // A^T q gather units: ceil(N / coefs_per_chunk)
   int32_t coefs_per_chunk;   // = workers / coef_lanes
   int32_t coef_lanes;        // threads per coefficient in the A^T q gather
+  int32_t coef_split;        // 1: grid-split A^T q gather (32 coefficients per chunk, warps over grids)
   int32_t workers;           // gather threads per block (block threads - 32)
   int32_t mats_smem;         // doubles of DCT matrices to stage in shared memory (0 = read global)
   int32_t n_mats;            // doubles in dct_mats

@@ -25,6 +25,8 @@ struct BlockTabs {
   int cachedA, cachedB, cachedW;
   int wbytes;           // entry values staged with the A / B units: 4 (FP32), 8 (FP64) or 0
   const double* mats;   // DCT matrices (shared copy or global)
+  void* cmb;            // grid-split A^T q gather: per-warp partials, [2][gather warps][32] doubles
+                        // (at the start of the dynamic shared memory), else nullptr
 };
 
 // Start (in ints, from the unit's pool offset) of a unit's staged entry
@@ -44,13 +46,16 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   const int nA = nru > tm.rank ? (nru - tm.rank + tm.G - 1) / tm.G : 0;
   const int nB = ncc > tm.rank ? (ncc - tm.rank + tm.G - 1) / tm.G : 0;
   const int nW = nwu > tm.rank ? (nwu - tm.rank + tm.G - 1) / tm.G : 0;
-  int off = 0;
+  // grid-split plans: the gather's partial sums first (the host sizes every
+  // launch to hold them)
+  int off = P.coef_split ? coef_combine_bytes(BT) : 0;
+  void* cmb = P.coef_split ? static_cast<void*>(dsm) : nullptr;
   const double* mats = P.dct_mats;
-  if (P.mats_smem > 0 && static_cast<int>(P.mats_smem * sizeof(double)) <= smem_bytes) {
-    double* m = reinterpret_cast<double*>(dsm);
+  if (P.mats_smem > 0 && off + static_cast<int>(P.mats_smem * sizeof(double)) <= smem_bytes) {
+    double* m = reinterpret_cast<double*>(dsm + off);
     for (int i = threadIdx.x; i < P.mats_smem; i += BT) m[i] = __ldg(P.dct_mats + i);
     mats = m;
-    off = P.mats_smem * static_cast<int>(sizeof(double));
+    off += P.mats_smem * static_cast<int>(sizeof(double));
   }
   int* hdrA = reinterpret_cast<int*>(dsm + off);
   int* hdrB = hdrA + 5 * nA;
@@ -151,6 +156,7 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
   T->cachedW = cachedW;
   T->wbytes = wbytes;
   T->mats = mats;
+  T->cmb = cmb;
 }
 
 // ---------------------------------------------------------------------------
@@ -200,6 +206,7 @@ __device__ __forceinline__ double dct_final_row(const DevPlan& P, const double* 
 // Gather units (worker threads = threads 32..BT-1; warp 0 reduces meanwhile)
 //   row unit u: rows ru_first[u] .. ru_first[u+1]-1, ru_lanes[u] lanes per row
 //   coef unit c: coefficients c*coefs_per_chunk ..., coef_lanes lanes each
+//     (grid-split plans: 32 coefficients, one lane in every gather warp)
 // ---------------------------------------------------------------------------
 // Row unit geometry: from the block's shared copy (k < cachedA) or global.
 struct RowUnit {
@@ -385,11 +392,15 @@ __device__ __forceinline__ void wide_row_combine(int wk, V* a, V* b, bool* lead)
 template <typename V, typename WT, bool SV, int EPC, typename Val>
 __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, const WT* __restrict__ w, int c, int k,
                                          int wk, int* m_out, bool* lead, Val val) {
-  const int L = P.coef_lanes;
+  // lanes per coefficient and their stride over the grids: L lanes of one
+  // warp (lane-split), or lane wk % 32 of every gather warp (grid-split:
+  // 32 consecutive coefficients per chunk, warp g takes grids g, g + NW, ...)
+  const bool split = P.coef_split != 0;
+  const int L = split ? P.workers >> 5 : P.coef_lanes;
   const int cpc = P.coefs_per_chunk;
-  const int mi = wk / L;
+  const int mi = split ? (wk & 31) : wk / L;
   const int m = c * cpc + mi;
-  const int lane = wk & (L - 1);
+  const int lane = split ? (wk >> 5) : (wk & (L - 1));
   const int* cr = k < T.cachedB ? T.pool + T.hdrB[k] : nullptr;
   const WT* wsm = (SV && cr && static_cast<int>(sizeof(WT)) == T.wbytes)
                       ? reinterpret_cast<const WT*>(T.pool + wt_start(T.hdrB[k], P.K * cpc))
@@ -414,10 +425,46 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
         if (idx[i] >= 0) acc = fma(static_cast<V>(wv[i]), v[i], acc);
     }
   }
-  acc = lane_group_sum(acc, L);
   *m_out = m;
+  if (split) {  // the warps' partials are added by coef_combine
+    *lead = false;
+    return acc;
+  }
+  acc = lane_group_sum(acc, L);
   *lead = (m < P.N) && lane == 0;
   return acc;
+}
+
+// Completes a coefficient gather of chunk number k of this block: in the
+// grid-split form, every gather warp's partial goes to shared memory and the
+// first gather warp adds them in warp order (lead on its 32 lanes); the
+// lane-split form has its sum already.  Called by every thread of the block
+// (warp 0 included) once per chunk; the two buffers alternate with k, so one
+// block barrier per chunk suffices.
+template <int NW, typename V>
+__device__ __forceinline__ V coef_combine(const DevPlan& P, const BlockTabs& T, V t, int k, int wk, int m,
+                                          bool* lead) {
+  if (!P.coef_split) return t;
+  V* buf = static_cast<V*>(T.cmb) + (k & 1) * NW * 32;
+  if (wk >= 0) buf[wk] = t;
+  __syncthreads();
+  V s = V(0);
+  if (wk >= 0 && wk < 32) {
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s += buf[w * 32 + wk];
+  }
+  *lead = wk >= 0 && wk < 32 && m < P.N;
+  return s;
+}
+
+// The thread that owns coefficient index m of chunk c (updates its vectors).
+__device__ __forceinline__ bool coef_owner(const DevPlan& P, int c, int wk, int* m) {
+  if (P.coef_split) {
+    *m = c * 32 + (wk & 31);
+    return wk >= 0 && wk < 32;
+  }
+  *m = c * P.coefs_per_chunk + wk / P.coef_lanes;
+  return (wk & (P.coef_lanes - 1)) == 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -571,10 +618,10 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
     }
     // ================= phase B: t = A^T q; {s, p} and x updated by the owner
     {
-      const int L = P.coef_lanes;
+      const int L = P.coef_split ? 1 : P.coef_lanes;  // lead lanes sit at multiples of L
       auto own_load = [&](int c, V2* o, XT* xo) {
-        const int m = c * P.coefs_per_chunk + wk / L;
-        if ((wk & (L - 1)) == 0 && m < P.N) {
+        int m = 0;
+        if (coef_owner(P, c, wk, &m) && m < P.N) {
           *o = ldcg(sp + m);
           *xo = ldcg(x + m);
         }
@@ -615,6 +662,7 @@ __device__ bool cg_normal(const DevPlan& P, Team& tm, const BlockTabs& T, const 
           own_load(c, &o, &xo);
           t = coef_gather<V, WT, SV, (8 << DEEP)>(P, T, wcm, c, k, wk, &m, &lead, [&](int i) { return q[i]; });
         }
+        t = coef_combine<NW>(P, T, t, k, wk, m, &lead);
         PT part = pzero_part(PT{});
         if (wk >= 0 && lead) {
           const V pn = first ? o.x : fma(beta, o.y, o.x);
@@ -906,6 +954,10 @@ __device__ bool pcg_normal_w(const DevPlan& P, Team& tm, const BlockTabs& T, dou
 template <int BT, bool SV, int DEEP>
 __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned char* dsm, int smem_bytes) {
   const DevPlan& P = *J.plan;
+  if (P.coef_split && smem_bytes < coef_combine_bytes(BT)) {  // the host sizes launches to hold them
+    if (threadIdx.x == 0) atomicExch(tm.err, static_cast<int>(FCT_ERR_INVALID_ARG));
+    return false;
+  }
   BlockTabs T;
   load_block_tabs<BT>(P, tm, dsm, smem_bytes, &T, J.precision == FCT_MIXED && P.n_w_units > 0 && P.s_init == nullptr,
                       SV ? (J.precision == FCT_MIXED ? 4 : 8) : 0);
@@ -956,6 +1008,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
       bool lead = false;
       double t = 0.0;
       if (wk >= 0) t = coef_gather<double, double, SV, (8 << DEEP)>(P, T, P.wcm, c, k, wk, &m, &lead, [&](int i) { return ldcg(P.b + i); });
+      t = coef_combine<BT / 32 - 1>(P, T, t, k, wk, m, &lead);
       double part = 0.0;
       if (lead) {
         stcg(P.sp + m, make_double2(t, 0.0));
@@ -1034,6 +1087,7 @@ __device__ bool solve_job(const SolveJob& J, Team& tm, double* red, unsigned cha
         double t = 0.0;
         if (wk >= 0)
           t = coef_gather<double, double, SV, (8 << DEEP)>(P, T, P.wcm, c, kc, wk, &m, &lead, [&](int i) { return ldcg(P.rres + i); });
+        t = coef_combine<BT / 32 - 1>(P, T, t, kc, wk, m, &lead);
         double part = 0.0;
         if (lead) {
           stcg(P.sp32 + m, make_float2(static_cast<float>(t * ci), 0.0f));

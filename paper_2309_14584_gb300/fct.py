@@ -54,6 +54,7 @@ class fct_options(ctypes.Structure):
         ("entries_per_lane", ctypes.c_int),
         ("plan_build", ctypes.c_int),
         ("tensor_dct", ctypes.c_int),
+        ("coef_split", ctypes.c_int),
     ]
 
 
@@ -86,6 +87,10 @@ class fct_plan_info(ctypes.Structure):
         ("device_bytes", ctypes.c_int64),
         ("normal_nnz", ctypes.c_int64),
         ("tensor_dct_grids", ctypes.c_int64),
+        ("coef_split", ctypes.c_int32),
+        ("row_units", ctypes.c_int32),
+        ("wide_rows", ctypes.c_int32),
+        ("coef_chunks", ctypes.c_int32),
     ]
 
     def as_dict(self):
