@@ -239,7 +239,9 @@ __device__ __forceinline__ void warp0_team_sum(const double* part, int n, double
   for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
     double t[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0;
+    for (int j = 0; j < 8; ++j) t[j] = ldcg(part + min(i0 + 32 * j, n - 1));  // every load issued
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? t[j] : 0.0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) v += t[j];  // lane order: part[lane], part[lane+32], ...
   }
@@ -256,7 +258,9 @@ __device__ __forceinline__ double warp0_sum(const double* part, int n) {
   for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
     double t[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : 0.0;
+    for (int j = 0; j < 8; ++j) t[j] = ldcg(part + min(i0 + 32 * j, n - 1));  // every load issued
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? t[j] : 0.0;
 #pragma unroll
     for (int j = 0; j < 8; ++j) v += t[j];
   }
@@ -276,7 +280,9 @@ __device__ __forceinline__ double warp0_sum(const float2* part, int n) {
   for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 8) {
     float2 t[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_float2(0.0f, 0.0f);
+    for (int j = 0; j < 8; ++j) t[j] = ldcg(part + min(i0 + 32 * j, n - 1));  // every load issued
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t[j] = i0 + 32 * j < n ? t[j] : make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < 8; ++j) acc[j] = df_add(acc[j], t[j]);
   }
@@ -291,7 +297,9 @@ __device__ __forceinline__ double2 warp0_sum(const double2* part, int n) {
   for (int i0 = threadIdx.x; i0 < n; i0 += 32 * 4) {
     double2 t[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t[j] = i0 + 32 * j < n ? ldcg(part + i0 + 32 * j) : make_double2(0.0, 0.0);
+    for (int j = 0; j < 4; ++j) t[j] = ldcg(part + min(i0 + 32 * j, n - 1));  // every load issued
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = i0 + 32 * j < n ? t[j] : make_double2(0.0, 0.0);
 #pragma unroll
     for (int j = 0; j < 4; ++j) v = padd(v, t[j]);
   }

@@ -269,27 +269,42 @@ __device__ __forceinline__ void row_gather_n(const DevPlan& P, const BlockTabs& 
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
-      int c[EPR];
-      WT wv[EPR];
+    if (g.cl) {
+      const int* cl = g.cl;
+      const WT* wp = ws ? static_cast<const WT*>(g.wt) : w + g.jbase;
+      for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+        int c[EPR];
+        WT wv[EPR];
 #pragma unroll
-      for (int i = 0; i < EPR; ++i) {
-        const int j = j0 + i * gl;
-        c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
-        wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
-      }
-      V v1[EPR], v2[EPR];
-#pragma unroll
-      for (int i = 0; i < EPR; ++i) {
-        v1[i] = c[i] >= 0 ? val1(c[i]) : V(0);
-        if (NV > 1) v2[i] = c[i] >= 0 ? val2(c[i]) : V(0);
-      }
-#pragma unroll
-      for (int i = 0; i < EPR; ++i)
-        if (c[i] >= 0) {
-          a1 = fma(static_cast<V>(wv[i]), v1[i], a1);
-          if (NV > 1) a2 = fma(static_cast<V>(wv[i]), v2[i], a2);
+        for (int i = 0; i < EPR; ++i) {
+          const int j = min(j0 + i * gl, jb - 1);
+          c[i] = cl[j];
+          wv[i] = ws ? wp[j] : __ldg(wp + j);
         }
+        V v[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) v[i] = val1(c[i]);
+#pragma unroll
+        for (int i = 0; i < EPR; ++i)
+          if (j0 + i * gl < jb) a1 = fma(static_cast<V>(wv[i]), v[i], a1);
+      }
+    } else {
+      for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+        int c[EPR];
+        WT wv[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) {
+          const int j = min(j0 + i * gl, jb - 1);
+          c[i] = __ldg(P.col + j);
+          wv[i] = __ldg(w + j);
+        }
+        V v[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) v[i] = val1(c[i]);
+#pragma unroll
+        for (int i = 0; i < EPR; ++i)
+          if (j0 + i * gl < jb) a1 = fma(static_cast<V>(wv[i]), v[i], a1);
+      }
     }
   }
   *out1 = lane_group_sum(a1, wide ? 32 : g.lc);
@@ -328,29 +343,48 @@ __device__ __forceinline__ void row_gather_sp(const DevPlan& P, const BlockTabs&
       ja = __ldg(P.rowptr + row);
       jb = __ldg(P.rowptr + row + 1);
     }
-    for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
-      int c[EPR];
-      WT wv[EPR];
+    if (g.cl) {
+      const int* cl = g.cl;
+      const WT* wp = ws ? static_cast<const WT*>(g.wt) : w + g.jbase;
+      for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+        int c[EPR];
+        WT wv[EPR];
 #pragma unroll
-      for (int i = 0; i < EPR; ++i) {
-        const int j = j0 + i * gl;
-        c[i] = j < jb ? (g.cl ? g.cl[j] : __ldg(P.col + j)) : -1;
-        wv[i] = j < jb ? (ws ? static_cast<const WT*>(g.wt)[j] : __ldg(w + g.jbase + j)) : WT(0);
-      }
-      V2 v[EPR];
-#pragma unroll
-      for (int i = 0; i < EPR; ++i) {
-        // plain (L1-cached) loads: {s, p} is written only in the phase before
-        // the last team barrier, whose acquire drops this SM's stale L1 lines
-        if (c[i] >= 0) v[i] = sp[c[i]];
-        else { v[i].x = V(0); v[i].y = V(0); }
-      }
-#pragma unroll
-      for (int i = 0; i < EPR; ++i)
-        if (c[i] >= 0) {
-          a1 = fma(static_cast<V>(wv[i]), v[i].x, a1);
-          if (!first) a2 = fma(static_cast<V>(wv[i]), v[i].y, a2);
+        for (int i = 0; i < EPR; ++i) {
+          const int j = min(j0 + i * gl, jb - 1);
+          c[i] = cl[j];
+          wv[i] = ws ? wp[j] : __ldg(wp + j);
         }
+        V2 v[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) v[i] = sp[c[i]];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i)
+          if (j0 + i * gl < jb) {
+            a1 = fma(static_cast<V>(wv[i]), v[i].x, a1);
+            if (!first) a2 = fma(static_cast<V>(wv[i]), v[i].y, a2);
+          }
+      }
+    } else {
+      for (int j0 = ja + lane; j0 < jb; j0 += EPR * gl) {
+        int c[EPR];
+        WT wv[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) {
+          const int j = min(j0 + i * gl, jb - 1);
+          c[i] = __ldg(P.col + j);
+          wv[i] = __ldg(w + j);
+        }
+        V2 v[EPR];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i) v[i] = sp[c[i]];
+#pragma unroll
+        for (int i = 0; i < EPR; ++i)
+          if (j0 + i * gl < jb) {
+            a1 = fma(static_cast<V>(wv[i]), v[i].x, a1);
+            if (!first) a2 = fma(static_cast<V>(wv[i]), v[i].y, a2);
+          }
+      }
     }
   }
   *as = lane_group_sum(a1, wide ? 32 : g.lc);
@@ -407,22 +441,44 @@ __device__ __forceinline__ V coef_gather(const DevPlan& P, const BlockTabs& T, c
                       : nullptr;
   V acc = V(0);
   if (m < P.N) {
+    const int K = P.K;
     const int64_t N = P.N;
-    for (int lb = lane; lb < P.K; lb += EPC * L) {
-      int idx[EPC];
-      WT wv[EPC];
+    if (cr == nullptr) {
+      const int* cg = P.crow + m;
+      const WT* wg = w + m;
+      for (int lb = lane; lb < K; lb += EPC * L) {
+        int idx[EPC];
+        WT wv[EPC];
 #pragma unroll
-      for (int i = 0; i < EPC; ++i) {
-        const int l = lb + i * L;
-        idx[i] = l < P.K ? (cr ? cr[l * cpc + mi] : __ldg(P.crow + l * N + m)) : -1;
-        wv[i] = l < P.K ? (wsm ? wsm[l * cpc + mi] : __ldg(w + l * N + m)) : WT(0);
+        for (int i = 0; i < EPC; ++i) {
+          const int64_t l = min(lb + i * L, K - 1);
+          idx[i] = __ldg(cg + l * N);
+          wv[i] = __ldg(wg + l * N);
+        }
+        V v[EPC];
+#pragma unroll
+        for (int i = 0; i < EPC; ++i) v[i] = val(idx[i]);
+#pragma unroll
+        for (int i = 0; i < EPC; ++i)
+          if (lb + i * L < K) acc = fma(static_cast<V>(wv[i]), v[i], acc);
       }
-      V v[EPC];
+    } else {
+      for (int lb = lane; lb < K; lb += EPC * L) {
+        int idx[EPC];
+        WT wv[EPC];
 #pragma unroll
-      for (int i = 0; i < EPC; ++i) v[i] = idx[i] >= 0 ? val(idx[i]) : V(0);
+        for (int i = 0; i < EPC; ++i) {
+          const int l = min(lb + i * L, K - 1);
+          idx[i] = cr[l * cpc + mi];
+          wv[i] = wsm ? wsm[l * cpc + mi] : __ldg(w + static_cast<int64_t>(l) * N + m);
+        }
+        V v[EPC];
 #pragma unroll
-      for (int i = 0; i < EPC; ++i)
-        if (idx[i] >= 0) acc = fma(static_cast<V>(wv[i]), v[i], acc);
+        for (int i = 0; i < EPC; ++i) v[i] = val(idx[i]);
+#pragma unroll
+        for (int i = 0; i < EPC; ++i)
+          if (lb + i * L < K) acc = fma(static_cast<V>(wv[i]), v[i], acc);
+      }
     }
   }
   *m_out = m;
