@@ -165,6 +165,10 @@ typedef struct {
   int32_t row_units;        /* A p gather units of the solver (each adds one partial sum) */
   int32_t wide_rows;        /* rows gathered by a whole block (the first row units)     */
   int32_t coef_chunks;      /* A^T q gather units of the solver                         */
+  int32_t entries_per_lane; /* A p gather: entries per lane of a row unit (2, 4 or 8)   */
+  int32_t kernel_variant;   /* solver kernel of fct_execute: 0 plain, 1 entry values staged
+                               in shared memory, 2 deep gathers (twice the entries per
+                               lane and round)                                          */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,

@@ -285,6 +285,7 @@ struct fct_plan_s {
   std::vector<int32_t> w_rowptr_h;          // row pointer of W = A^T A (empty when not built)
   bool stage_values = false;                // single launches stage the CG loop's entry values too
   int kernel_kind = 0;                      // solver kernel variant of single launches (kKernel*)
+  int entries_per_lane = 0;                 // A p gather: entries per lane of a row unit
   double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
   // DCT passes on the tensor cores (grids with a long axis; null when none):
@@ -389,6 +390,34 @@ size_t team_smem_need(const fct_plan P, int G, bool with_values) {
 // the index tables (batches, serving, the condition probe).
 size_t launch_smem(const fct_plan P, int G, size_t cap) { return std::min(team_smem_need(P, G, false), cap); }
 
+// Dynamic shared memory a solver block may take without lowering the blocks
+// per SM of the plain kernel (the largest static shared memory of the
+// kernel variants counted), set as every variant's limit.  Plans and servers
+// of one block size compute the same value, so neither lowers the other's
+// launch limit.
+fct_status solver_smem_cap(int bt, const cudaDeviceProp& prop, int* cap_out, int* per_sm_out) {
+  const void* kfn = solve_kernel_for(bt);
+  cudaFuncAttributes fa;
+  FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
+  for (int kind : {kKernelStaged, kKernelDeep}) {
+    cudaFuncAttributes fk;
+    FCT_CUDA(cudaFuncGetAttributes(&fk, solve_kernel_for(bt, kind)));
+    fa.sharedSizeBytes = std::max(fa.sharedSizeBytes, fk.sharedSizeBytes);
+  }
+  int per_sm = 0;
+  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, bt, 0));
+  if (per_sm < 1) return fail(FCT_ERR_CUDA, "solver kernel cannot be resident");
+  const int reserve = 1024;  // per-block system reservation
+  int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / per_sm) - reserve - static_cast<int>(fa.sharedSizeBytes);
+  cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
+  cap = std::max(cap, 0) & ~15;
+  for (int kind : {kKernelPlain, kKernelStaged, kKernelDeep})
+    FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(bt, kind), cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  *cap_out = cap;
+  *per_sm_out = per_sm;
+  return FCT_OK;
+}
+
 fct_status choose_shape(fct_plan P) {
   int dev = 0;
   FCT_CUDA(cudaGetDevice(&dev));
@@ -396,28 +425,11 @@ fct_status choose_shape(fct_plan P) {
   FCT_CUDA(cudaGetDeviceProperties(&prop, dev));
   if (!prop.cooperativeLaunch) return fail(FCT_ERR_CUDA, "device does not support cooperative launch");
   const void* kfn = solve_kernel_for(P->block_threads);
-  cudaFuncAttributes fa;
-  FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
-  for (int kind : {kKernelStaged, kKernelDeep}) {  // the largest static shared memory of the variants
-    cudaFuncAttributes fk;
-    FCT_CUDA(cudaFuncGetAttributes(&fk, solve_kernel_for(P->block_threads, kind)));
-    fa.sharedSizeBytes = std::max(fa.sharedSizeBytes, fk.sharedSizeBytes);
-  }
-  int per_sm = 0;
-  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, P->block_threads, 0));
-  if (per_sm < 1) return fail(FCT_ERR_CUDA, "solver kernel cannot be resident");
-  // shared memory each block may take without lowering the blocks per SM
-  const int reserve = 1024;  // per-block system reservation
-  int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / per_sm) - reserve - static_cast<int>(fa.sharedSizeBytes);
-  cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
-  cap = std::max(cap, 0) & ~15;
+  int cap = 0, per_sm = 0;
+  const fct_status cs = solver_smem_cap(P->block_threads, prop, &cap, &per_sm);
+  if (cs != FCT_OK) return cs;
   if (P->hp.coef_split && cap < coef_combine_bytes(P->block_threads))
     return fail(FCT_ERR_CUDA, "no shared memory for the grid-split gather");
-  FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, kKernelStaged),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
-  FCT_CUDA(cudaFuncSetAttribute(solve_kernel_for(P->block_threads, kKernelDeep),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   P->blocks_per_sm = per_sm;
   P->smem_cap = cap;
   P->max_coresident = per_sm * prop.multiProcessorCount;
@@ -610,6 +622,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   hp.n_rowel_chunks = static_cast<int32_t>((H.R + BT - 1) / BT);
   std::vector<int32_t> ru_first, ru_lanes, rowbase, rowk;
   row_units(H, workers, epl, &ru_first, &ru_lanes);
+  P->entries_per_lane = epl;
   if (!on_device) final_pass_rows(H, &rowbase, &rowk);  // the device build made them
   hp.n_row_units = static_cast<int32_t>(ru_lanes.size());
   hp.n_wide_units = 0;
@@ -897,6 +910,8 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->row_units = P->hp.n_row_units;
   info->wide_rows = P->hp.n_wide_units;
   info->coef_chunks = P->hp.n_coef_chunks;
+  info->entries_per_lane = P->entries_per_lane;
+  info->kernel_variant = P->kernel_kind;
   info->tensor_dct_grids = 0;
   if (P->tc)
     for (char g : P->tc->grid_tc) info->tensor_dct_grids += g ? 1 : 0;
@@ -1585,20 +1600,14 @@ fct_status fct_server_create(fct_server* out, int block_threads, int team_blocks
   if (block_threads != 128 && block_threads != 256 && block_threads != 512)
     return fail(FCT_ERR_INVALID_ARG, "block_threads must be 128, 256 or 512");
   if (!(idle_timeout_s > 0.0) || idle_timeout_s > 1.0) return fail(FCT_ERR_INVALID_ARG, "idle_timeout_s must be in (0, 1]");
-  int dev = 0, nsm = 0, per_sm = 0;
+  int dev = 0, nsm = 0, per_sm = 0, cap = 0;
   FCT_CUDA(cudaGetDevice(&dev));
   FCT_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const void* kfn = solve_kernel_for(block_threads);
-  FCT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, block_threads, 0));
   cudaDeviceProp prop;
   FCT_CUDA(cudaGetDeviceProperties(&prop, dev));
-  cudaFuncAttributes fa;
-  FCT_CUDA(cudaFuncGetAttributes(&fa, kfn));
-  int cap = static_cast<int>(prop.sharedMemPerMultiprocessor / std::max(per_sm, 1)) - 1024 -
-            static_cast<int>(fa.sharedSizeBytes);
-  cap = std::min(cap, static_cast<int>(prop.sharedMemPerBlockOptin) - static_cast<int>(fa.sharedSizeBytes));
-  cap = std::max(cap, 0) & ~15;
-  FCT_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  const fct_status cs = solver_smem_cap(block_threads, prop, &cap, &per_sm);
+  if (cs != FCT_OK) return cs;
+  if (cap < coef_combine_bytes(block_threads)) return fail(FCT_ERR_CUDA, "no shared memory for the solver");
   const int coresident = per_sm * nsm;
   if (team_blocks <= 0) team_blocks = 16;
   team_blocks = std::min(team_blocks, coresident);

@@ -91,6 +91,8 @@ class fct_plan_info(ctypes.Structure):
         ("row_units", ctypes.c_int32),
         ("wide_rows", ctypes.c_int32),
         ("coef_chunks", ctypes.c_int32),
+        ("entries_per_lane", ctypes.c_int32),
+        ("kernel_variant", ctypes.c_int32),
     ]
 
     def as_dict(self):

@@ -85,6 +85,43 @@ def test_jobs_submitted_while_others_run_join_them():
         p.close()
 
 
+def test_plans_built_while_the_server_runs_are_served():
+    """Plans are built on a stream of their own, so a plan created while a
+    serving launch holds part of the device is served at once (a plan-cache
+    miss), with the coefficients of the same transform alone.  Plans and
+    servers of one block size use one shared-memory limit, so a plan built
+    later cannot lower the running server's launch limit."""
+    long_w = W.config_d10_rational()
+    pl = F.Plan(long_w.support, long_w.sizes, long_w.nodes, precision=F.FCT_FP64, tol=1e-13)
+    xl = torch.empty(pl.M, dtype=torch.float64, device="cuda")
+    pl.sample(long_w.family, long_w.params, xl)
+    ol = torch.empty(pl.N, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    srv = F.fct_server_create(0, 16, 4, 0.2)  # 4 teams of 16 blocks: most SMs stay free
+    tl = F.fct_server_submit(srv, pl.handle, xl, ol)
+    jobs = []
+    for i, w in enumerate(_shapes()):
+        p = F.Plan(w.support, w.sizes, w.nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-5)
+        x = torch.empty(p.M, dtype=torch.float64, device="cuda")
+        p.sample(W.FAMILY_GAUSSCOS, W.gausscos_params(40 + i, w.D), x)
+        o = torch.full((p.N,), float("nan"), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        jobs.append((p, x, o, F.fct_server_submit(srv, p.handle, x, o)))
+    for _, _, _, t in jobs:
+        assert F.fct_server_wait(srv, t, 60.0)["status"] == 0
+    assert F.fct_server_wait(srv, tl, 120.0)["status"] == 0
+    F.fct_server_destroy(srv)
+    for p, x, o, _ in jobs:
+        alone = torch.empty_like(o)
+        assert p.execute(x, alone)["status"] == 0
+        assert torch.equal(alone, o)
+        p.close()
+    alone = torch.empty_like(ol)
+    assert pl.execute(xl, alone)["status"] == 0
+    assert torch.equal(alone, ol)
+    pl.close()
+
+
 def test_teams_stay_while_a_long_job_runs():
     """The server is left idle longer than its idle timeout while one long
     transform runs on one team; short jobs submitted afterwards still run on
