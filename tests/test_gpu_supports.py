@@ -85,6 +85,27 @@ def test_sparse_support_D100_large_exact_recovery():
     assert rel(c.cpu().numpy(), c_true) <= 1e-10
 
 
+@pytest.mark.slow
+def test_sparse_support_D100_N1e6_exact_recovery():
+    """The paper's sparse-support scale: 10^6 random multi-indices at D = 100
+    (10 nonzero components of degree <= 3 each), 400 grids by Algorithm 1
+    (K N = 4e8 table entries, M = 8.1e8 samples); a polynomial on that support
+    is recovered by the mixed path (the check that holds at any size)."""
+    D, d, N, K = 100, 3, 1_000_000, 400
+    sup = W.sparse_support_vectorised(3, D, d, N, 10)
+    sizes, nodes = W.l_grid(500, N, D, K, 1, d + 1)
+    c_true = W.poly_coefficients(10, sup)
+    plan = F.Plan(sup, sizes, nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4, block_threads=512)
+    assert plan.info["nnz"] == K * N
+    x = torch.empty(plan.M, dtype=torch.float64, device="cuda")
+    plan.sample(W.FAMILY_POLY | F.fct.FCT_SAMPLE_FOLDED, c_true, x)
+    c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
+    rep = plan.execute(x, c)
+    plan.close()
+    assert rep["status"] == 0, rep
+    assert rel(c.cpu().numpy(), c_true) <= 1e-10
+
+
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_wide_rows_match_oracle_and_batch(bt):
     """Sparse supports put most columns in bin 0 of a grid: rows of more than

@@ -38,6 +38,7 @@ _PURPOSE = {
     "arrivals": 6,   # serving arrival process
     "probe": 7,      # start vectors of condition probes and test matrices
     "support": 8,    # random sparse supports
+    "support_vec": 9,  # random sparse supports drawn in vectorised batches
 }
 
 
@@ -102,6 +103,35 @@ def sparse_infinity_support(seed: int, D: int, d: int, N: int, nonzeros: int) ->
     arr = np.stack(out)
     order = np.lexsort(arr.T[::-1])
     return arr[order].astype(np.uint16)
+
+
+def sparse_support_vectorised(seed: int, D: int, d: int, N: int, nonzeros: int) -> np.ndarray:
+    """N distinct multi-indices of S^inf_{d,D}: the zero index, then indices with
+    exactly `nonzeros` nonzero components at uniformly drawn axes with values
+    uniform in {1..d}, in the order they were drawn (duplicates dropped).  The
+    same family as sparse_infinity_support, drawn in vectorised batches for
+    supports of 1e5..1e7 indices (a different random sequence)."""
+    g = stream(seed, "support_vec")
+    rows = [np.zeros((1, 2 * nonzeros), dtype=np.uint8)]
+    have = 1
+    while have < N:
+        n = int((N - have) * 1.2) + 1024
+        keys = g.random((n, D), dtype=np.float32)
+        axes = np.sort(np.argpartition(keys, nonzeros, axis=1)[:, :nonzeros], axis=1)
+        vals = g.integers(1, d + 1, size=(n, nonzeros))
+        rows.append(np.hstack([axes, vals]).astype(np.uint8))
+        allr = np.ascontiguousarray(np.vstack(rows))
+        view = allr.view(np.dtype((np.void, allr.shape[1]))).ravel()
+        _, first = np.unique(view, return_index=True)
+        keep = np.sort(first)
+        rows = [allr[keep]]
+        have = len(keep)
+    sel = rows[0][:N]
+    out = np.zeros((N, D), dtype=np.uint16)
+    r = np.arange(1, N)
+    for j in range(nonzeros):
+        out[r, sel[1:, j].astype(np.int64)] = sel[1:, nonzeros + j]
+    return out
 
 
 # --------------------------------------------------------------------------
