@@ -185,16 +185,19 @@ const char* fct_status_string(int status);
  * Build a plan: the alias tables of every grid (Sec. 3.3, Algorithm 2 without
  * its condition-number loop; the L-grid is an input; built by kernels on the
  * current device unless opt->plan_build says host), the DCT-I matrices and the
- * solver workspace, all resident on the current device.  The device build
- * frees its scratch before returning, which waits for all work on the device
- * (a running fct_server launch included): create plans before starting a
- * server, as the serving engine does.
+ * solver workspace, all resident on the current device.  Every launch, copy,
+ * scratch allocation (cudaMallocAsync) and release of the build is ordered on
+ * a stream the call creates for itself, and only that stream is waited for,
+ * so a plan can be built while other streams keep the device busy (e.g. a
+ * running fct_server launch whose teams leave SMs free: a plan-cache miss
+ * while serving).  The plan's tables and workspace are one cudaMalloc (two
+ * with tensor-core grids).
  *   D in [1, 255]; N >= 1; support host uint16[N][D] (any multi-indices);
  *   K >= 1; sizes host int32[K][D], every n in [1, 4096], each grid's point count and
  *   the total M below 2^31, K*N below 2^31; nodes host double[K][D] in [-1,1]
  *   (read where n == 1; NULL means xi = 1); opt NULL = defaults.
- * Synchronous.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_OOM, FCT_ERR_CUDA,
- * FCT_ERR_NO_DEVICE.  *out is NULL on failure.
+ * Returns when the plan is ready.  Errors: FCT_ERR_INVALID_ARG, FCT_ERR_OOM,
+ * FCT_ERR_CUDA, FCT_ERR_NO_DEVICE.  *out is NULL on failure.
  */
 fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* support,
                            int K, const int32_t* sizes, const double* nodes,
