@@ -761,6 +761,7 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
     import torch
     import workloads as W
     out = {}
+    peaks, peak_kind = measured_peaks()
     # first-kind grid (1/n DCT-II quadrature, signed alias entries), same workload and options
     p = F.Plan(w.support, w.sizes, w.nodes, grid_kind=F.FCT_GRID_FIRST_KIND, **opts)
     x = torch.empty(p.M, dtype=torch.float64, device="cuda")
@@ -802,6 +803,17 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
                     "iterations": rep["iterations"]}
         if mode == 0:
             c_on = ct.cpu().numpy()
+            # tensor roof of the DCT stage (its GEMMs, digit splits and last pass together):
+            # BF16 flops the passes issue against the measured dense BF16 rate
+            flops = pt.info["tensor_dct_flops"]
+            peak = peaks.get("bf16_tflops")
+            row[key]["tensor_roofline"] = {
+                "bound": "tensor", "flops_per_transform": flops, "unit": "TFLOP/s",
+                "achieved": flops / (rhs_ms / 1e3) / 1e12, "peak": peak,
+                "frac": flops / (rhs_ms / 1e3) / 1e12 / peak if peak else None,
+                "peak_kind": f"{peak_kind} BF16 dense (cuBLAS burst), MEASURED_PEAKS.json",
+                "note": "flops of the 36 exact digit-slice products per tile and K step over the whole DCT "
+                        "stage time (fct_plan_rhs); the useful FP64 DCT work is 36x smaller"}
         else:
             row["rel_diff_on_off"] = float(np.linalg.norm(c_on - ct.cpu().numpy()) / np.linalg.norm(ct.cpu().numpy()))
         pt.close()

@@ -169,6 +169,9 @@ typedef struct {
   int32_t kernel_variant;   /* solver kernel of fct_execute: 0 plain, 1 entry values staged
                                in shared memory, 2 deep gathers (twice the entries per
                                lane and round)                                          */
+  int64_t tensor_dct_flops; /* BF16 tensor-core flops of the DCT passes per fct_execute
+                               (36 digit-slice products of M 128 x N 64 x K 16 per tile
+                               and K step); 0 without tensor-core grids              */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,

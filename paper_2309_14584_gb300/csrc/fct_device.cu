@@ -913,8 +913,14 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->entries_per_lane = P->entries_per_lane;
   info->kernel_variant = P->kernel_kind;
   info->tensor_dct_grids = 0;
-  if (P->tc)
+  info->tensor_dct_flops = 0;
+  if (P->tc) {
     for (char g : P->tc->grid_tc) info->tensor_dct_grids += g ? 1 : 0;
+    // every GEMM tile issues 36 digit-slice products (M 128, N 64, K 16) per K step
+    const int64_t per_step = 36ll * 2 * kTcM * kTcN * kTcK;
+    for (size_t t = 0; t + 3 < P->tc->gemm_tasks.size(); t += 4)
+      info->tensor_dct_flops += per_step * P->tc->gp[P->tc->gemm_tasks[t]].ksteps;
+  }
   return FCT_OK;
 }
 

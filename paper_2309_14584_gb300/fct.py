@@ -93,6 +93,7 @@ class fct_plan_info(ctypes.Structure):
         ("coef_chunks", ctypes.c_int32),
         ("entries_per_lane", ctypes.c_int32),
         ("kernel_variant", ctypes.c_int32),
+        ("tensor_dct_flops", ctypes.c_int64),
     ]
 
     def as_dict(self):

@@ -85,6 +85,10 @@ def test_tensor_core_grid_selection():
     sup, sizes, nodes = _case("D3_mid")
     p = F.Plan(sup, sizes, nodes)
     assert p.info["tensor_dct_grids"] == 3   # 70, 80 and 100 points; the 14-point grid stays
+    assert p.info["tensor_dct_flops"] > 0 and p.info["tensor_dct_flops"] % (36 * 2 * 128 * 64 * 16) == 0
+    p.close()
+    p = F.Plan(sup, sizes, nodes, tensor_dct=-1)
+    assert p.info["tensor_dct_grids"] == 0 and p.info["tensor_dct_flops"] == 0
     p.close()
     p = F.Plan(sup, sizes, nodes, tensor_dct=1)
     assert p.info["tensor_dct_grids"] == 4
