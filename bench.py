@@ -872,6 +872,32 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
     return out
 
 
+def _graph_batch(F, hs, xs, cs, tb, steps, flush):
+    """The same batch as a prepared batch (fct_batch_create) whose launch is
+    captured once into a CUDA graph and replayed: per replay one memset and one
+    cooperative launch, nothing from the host.  Returns the replay times (ms),
+    whether the replay's coefficients equal the direct launch's bit for bit,
+    and whether every report is FCT_OK."""
+    import torch
+    ref = [c.clone() for c in cs]
+    b = F.fct_batch_create(hs, xs, cs, team_blocks=tb)
+    try:
+        F.fct_batch_launch(b)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            F.fct_batch_launch(b)
+        g.replay()
+        torch.cuda.synchronize()
+        ok = all(r["status"] == 0 for r in F.fct_batch_reports(b, len(hs)))
+        same = all(bool(torch.equal(c, r)) for c, r in zip(cs, ref))
+        ms = _timed(lambda: g.replay(), steps, flush)
+        del g
+    finally:
+        F.fct_batch_destroy(b)
+    return ms, same, ok
+
+
 def run_batched(args, F, w, opts, flush) -> dict:
     """B transforms of workload w (distinct Gaussian-cosine targets, one plan
     and B - 1 clones) per launch of fct_execute_batch, the blocks per team
@@ -898,10 +924,14 @@ def run_batched(args, F, w, opts, flush) -> dict:
     for _ in range(args.warmup):
         F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False)
     ms = _timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), args.steps, flush)
+    gms, gsame, gok = _graph_batch(F, hs, xs, cs, tb, args.steps, flush)
     for p in plans[1:]:
         p.close()
     base.close()
     return {"workload": w.name, "transforms_per_launch": B, "team_blocks": tb,
+            "graph": {"ms_per_launch": statistics.mean(gms), "value": B * w.N / (statistics.mean(gms) / 1e3),
+                      "equals_direct_launch": gsame, "all_converged": gok,
+                      "note": "fct_batch_launch captured into a CUDA graph, replayed"},
             "team_blocks_tuning_ms": [[t, round(m, 3)] for t, m in tune["timings"]], "path": "mixed",
             "coeffs_per_launch": B * w.N, "ms_per_launch": statistics.mean(ms), "total_s": sum(ms) / 1e3, "ms": ms,
             "all_converged": all(r["status"] == 0 for r in reps),
@@ -951,10 +981,15 @@ def run_hetero_batch(args, F, opts) -> dict:
     plans[small].execute(xs[small], alone)
     same = bool(torch.equal(alone, cs[small]))
     checks = [(f"hetero:{ws[i].name}", ws[i], cs[i].cpu().numpy()) for i in order[:HETERO_CHECKED]]
-    ms = statistics.mean(_timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), 2,
-                                torch.empty(1, device="cuda")))
+    direct_ms = statistics.mean(_timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), 2,
+                                       torch.empty(1, device="cuda")))
+    gms, gsame, gok = _graph_batch(F, hs, xs, cs, tb, 2, torch.empty(1, device="cuda"))
+    ms = statistics.mean(gms)
     sum_n = sum(p.N for p in plans)
     out = {"transforms_per_launch": len(plans), "value": sum_n / (ms / 1e3), "unit": UNIT, "ms_per_launch": ms,
+           "launch": "one persistent cooperative launch per step, captured once into a CUDA graph and replayed "
+                     "(fct_batch_launch)", "direct_ms_per_launch": direct_ms, "graph_equals_direct_launch": gsame,
+           "graph_all_converged": gok,
            "coeffs_per_launch": sum_n, "samples_per_launch": sum(p.M for p in plans), "timed_launches": 2,
            "grid_selection_s": round(t_select, 1),
            "grid_count_over_3D_median": sorted(L / (3 * w.D) for L, w in zip(Ls, cands))[len(Ls) // 2],

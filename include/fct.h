@@ -267,6 +267,33 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
                              fct_report* reps);
 
 /*
+ * A prepared batch: the job table of fct_execute_batch kept in device memory,
+ * so that the launch itself needs nothing from the host.
+ *   fct_batch_create: same arguments and rules as fct_execute_batch (the
+ *     buffers and plans are bound to the batch; the caller keeps them alive
+ *     and does not run those plans elsewhere while a launch of the batch is
+ *     in flight).  Allocates the job table, the reports and a launch state,
+ *     uploads the jobs and fixes the launch shape.  Synchronous.
+ *   fct_batch_launch: one memset of the launch state and one cooperative
+ *     launch (cudaLaunchKernelEx with the cooperative attribute) on stream;
+ *     no host synchronisation, allocation or read of host memory, so the call
+ *     can be recorded by stream capture into a CUDA graph and the graph
+ *     replayed; every launch reads the samples as they are at its start and
+ *     writes the coefficients and the device-side reports.
+ *   fct_batch_reports: copies the B reports of the last completed launch into
+ *     host fct_report[B] after waiting for stream; returns the worst status,
+ *     or the launch's error code when a bounded device-side wait expired.
+ *   fct_batch_destroy: waits for the device, frees the batch (not the plans).
+ * Results are bit-identical to fct_execute_batch and to each transform alone.
+ */
+typedef struct fct_batch_s* fct_batch;
+fct_status fct_batch_create(fct_batch* out, int B, const fct_plan* plans, const double* const* samples,
+                            double* const* coeffs, int team_blocks);
+fct_status fct_batch_launch(fct_batch batch, void* stream);
+fct_status fct_batch_reports(fct_batch batch, void* stream, fct_report* reps);
+fct_status fct_batch_destroy(fct_batch batch);
+
+/*
  * fct_execute without any device allocation.  No counterpart in the paper: it
  * exists for callers that cannot allocate device memory when they solve, such
  * as code under a memory policy that forbids cudaMalloc after start-up (a

@@ -1125,8 +1125,12 @@ fct_status fct_execute_host(fct_plan P, const double* samples_host, double* coef
   return FCT_OK;
 }
 
-fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* samples, double* const* coeffs,
-                             int team_blocks, void* stream, fct_report* reps) {
+// Checks a batch, orders its jobs (largest transforms first: the shortest
+// tail for the device work queue) with each job's report at reports + i, and
+// fixes the launch shape: blocks per team G, teams, dynamic shared memory.
+static fct_status batch_setup(int B, const fct_plan* plans, const double* const* samples, double* const* coeffs,
+                              int team_blocks, fct_report* reports, std::vector<SolveJob>* jobs, int* G_out,
+                              int* teams_out, int* smem_out) {
   if (B < 1 || !plans || !samples || !coeffs) return fail(FCT_ERR_INVALID_ARG, "bad batch arguments");
   for (int i = 0; i < B; ++i) {
     if (!plans[i] || !samples[i] || !coeffs[i]) return fail(FCT_ERR_INVALID_ARG, "NULL plan or buffer in batch");
@@ -1136,31 +1140,16 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
       return fail(FCT_ERR_INVALID_ARG, "all plans of a batch must use the same block_threads");
   }
   fct_plan P0 = plans[0];
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  // the batch's job array and reports live in plan 0's memory
-  if (P0->djobs_cap < B) {
-    if (P0->djobs) {
-      FCT_CUDA(cudaStreamSynchronize(st));
-      cudaFree(P0->djobs);
-    }
-    FCT_CUDA(cudaMalloc(&P0->djobs, (sizeof(SolveJob) + sizeof(fct_report)) * B));
-    P0->djobs_cap = B;
-  }
-  fct_report* dreps = reinterpret_cast<fct_report*>(P0->djobs + P0->djobs_cap);
-  // Queue order: largest transforms first (longest-processing-time-first keeps
-  // the tail short); each job still writes its own caller's report slot.
   std::vector<int> order(B);
   for (int i = 0; i < B; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
     return plans[a]->hp.K * static_cast<int64_t>(plans[a]->N) > plans[b]->hp.K * static_cast<int64_t>(plans[b]->N);
   });
-  std::vector<SolveJob> jobs(B);
+  jobs->assign(B, SolveJob{});
   for (int q = 0; q < B; ++q) {
     const int i = order[q];
-    jobs[q] = make_job(plans[i], samples[i], coeffs[i], dreps + i);
+    (*jobs)[q] = make_job(plans[i], samples[i], coeffs[i], reports + i);
   }
-  FCT_CUDA(cudaMemcpyAsync(P0->djobs, jobs.data(), sizeof(SolveJob) * B, cudaMemcpyHostToDevice, st));
-  FCT_CUDA(cudaStreamSynchronize(st));
   int G = team_blocks;
   if (G <= 0) {
     int units = 0;
@@ -1168,20 +1157,146 @@ fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* 
     G = std::max(1, std::min(units, P0->max_coresident / std::max(1, std::min(B, 16))));
   }
   G = std::min(G, P0->max_coresident);
-  int teams = std::min(std::max(1, P0->max_coresident / G), std::min(B, kMaxTeams));
+  *teams_out = std::min(std::max(1, P0->max_coresident / G), std::min(B, kMaxTeams));
+  *G_out = G;
+  size_t need = 0;
+  for (int i = 0; i < B; ++i) need = std::max(need, launch_smem(plans[i], G, static_cast<size_t>(P0->smem_cap)));
+  *smem_out = std::min(static_cast<int>(std::min<size_t>(need, P0->smem_cap) + 15) & ~15, P0->smem_cap);
+  return FCT_OK;
+}
+
+fct_status fct_execute_batch(int B, const fct_plan* plans, const double* const* samples, double* const* coeffs,
+                             int team_blocks, void* stream, fct_report* reps) {
+  if (B < 1 || !plans || !plans[0]) return fail(FCT_ERR_INVALID_ARG, "bad batch arguments");
+  fct_plan P0 = plans[0];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the batch's job array and reports live in plan 0's memory
+  if (P0->djobs_cap < B) {
+    if (P0->djobs) {
+      FCT_CUDA(cudaStreamSynchronize(st));
+      cudaFree(P0->djobs);
+      P0->djobs = nullptr;
+      P0->djobs_cap = 0;
+    }
+    FCT_CUDA(cudaMalloc(&P0->djobs, (sizeof(SolveJob) + sizeof(fct_report)) * B));
+    P0->djobs_cap = B;
+  }
+  fct_report* dreps = reinterpret_cast<fct_report*>(P0->djobs + P0->djobs_cap);
+  std::vector<SolveJob> jobs;
+  int G = 0, teams = 0, smem = 0;
+  fct_status s = batch_setup(B, plans, samples, coeffs, team_blocks, dreps, &jobs, &G, &teams, &smem);
+  if (s != FCT_OK) return s;
+  FCT_CUDA(cudaMemcpyAsync(P0->djobs, jobs.data(), sizeof(SolveJob) * B, cudaMemcpyHostToDevice, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
   SolveArgs a{};
   a.jobs = P0->djobs;
   a.njobs = B;
   a.team_blocks = G;
   a.ls = P0->ls;
   a.timeout_ns = timeout_ns(P0);
-  size_t need = 0;
-  for (int i = 0; i < B; ++i) need = std::max(need, launch_smem(plans[i], G, static_cast<size_t>(P0->smem_cap)));
-  a.smem_bytes = static_cast<int>(std::min<size_t>(need, P0->smem_cap) + 15) & ~15;
-  a.smem_bytes = std::min(a.smem_bytes, P0->smem_cap);
-  fct_status s = launch_solve(P0, a, teams * G, st);
+  a.smem_bytes = smem;
+  s = launch_solve(P0, a, teams * G, st);
   if (s != FCT_OK) return s;
   if (reps) return read_report(P0, dreps, st, reps, B);
+  return FCT_OK;
+}
+
+}  // extern "C"
+
+struct fct_batch_s {
+  int B = 0, G = 0, teams = 0, smem = 0, block_threads = 0, device = 0;
+  unsigned long long tns = 0;
+  SolveJob* djobs = nullptr;   // [B] jobs, then [B] reports
+  fct_report* dreps = nullptr;
+  LaunchState* ls = nullptr;
+};
+
+extern "C" {
+
+fct_status fct_batch_create(fct_batch* out, int B, const fct_plan* plans, const double* const* samples,
+                            double* const* coeffs, int team_blocks) {
+  if (!out) return fail(FCT_ERR_INVALID_ARG, "out must not be NULL");
+  *out = nullptr;
+  if (B < 1 || !plans || !plans[0]) return fail(FCT_ERR_INVALID_ARG, "bad batch arguments");
+  auto* Bt = new fct_batch_s();
+  auto fail_free = [&](fct_status st) {
+    if (Bt->djobs) cudaFree(Bt->djobs);
+    if (Bt->ls) cudaFree(Bt->ls);
+    delete Bt;
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&Bt->djobs, (sizeof(SolveJob) + sizeof(fct_report)) * B);
+  if (e == cudaSuccess) e = cudaMalloc(&Bt->ls, sizeof(LaunchState));
+  if (e == cudaSuccess) e = cudaMemset(Bt->ls, 0, sizeof(LaunchState));
+  if (e != cudaSuccess) return fail_free(cuda_fail(e, "fct_batch_create"));
+  Bt->dreps = reinterpret_cast<fct_report*>(Bt->djobs + B);
+  e = cudaMemset(Bt->dreps, 0, sizeof(fct_report) * B);
+  if (e != cudaSuccess) return fail_free(cuda_fail(e, "fct_batch_create"));
+  std::vector<SolveJob> jobs;
+  fct_status s = batch_setup(B, plans, samples, coeffs, team_blocks, Bt->dreps, &jobs, &Bt->G, &Bt->teams, &Bt->smem);
+  if (s != FCT_OK) return fail_free(s);
+  e = cudaMemcpy(Bt->djobs, jobs.data(), sizeof(SolveJob) * B, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail_free(cuda_fail(e, "fct_batch_create"));
+  Bt->B = B;
+  Bt->block_threads = plans[0]->block_threads;
+  Bt->device = plans[0]->device;
+  Bt->tns = timeout_ns(plans[0]);
+  *out = Bt;
+  return FCT_OK;
+}
+
+fct_status fct_batch_launch(fct_batch Bt, void* stream) {
+  if (!Bt) return fail(FCT_ERR_INVALID_ARG, "NULL batch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the whole launch state starts from zero (queue head, error flag, team
+  // barriers), also after an abandoned launch
+  FCT_CUDA(cudaMemsetAsync(Bt->ls, 0, sizeof(LaunchState), st));
+  SolveArgs a{};
+  a.jobs = Bt->djobs;
+  a.njobs = Bt->B;
+  a.team_blocks = Bt->G;
+  a.ls = Bt->ls;
+  a.timeout_ns = Bt->tns;
+  a.smem_bytes = Bt->smem;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(Bt->teams * Bt->G);
+  cfg.blockDim = dim3(Bt->block_threads);
+  cfg.dynamicSmemBytes = static_cast<size_t>(Bt->smem);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* kargs[] = {&a};
+  FCT_CUDA(cudaLaunchKernelExC(&cfg, solve_kernel_for(Bt->block_threads), kargs));
+  return FCT_OK;
+}
+
+fct_status fct_batch_reports(fct_batch Bt, void* stream, fct_report* reps) {
+  if (!Bt || !reps) return fail(FCT_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int err = 0;
+  FCT_CUDA(cudaMemcpyAsync(reps, Bt->dreps, sizeof(fct_report) * Bt->B, cudaMemcpyDeviceToHost, st));
+  FCT_CUDA(cudaMemcpyAsync(&err, &Bt->ls->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FCT_CUDA(cudaStreamSynchronize(st));
+  if (err != 0) {
+    for (int i = 0; i < Bt->B; ++i) reps[i].status = err;
+    return fail(static_cast<fct_status>(err), "device-side wait expired in the solver");
+  }
+  fct_status worst = FCT_OK;
+  for (int i = 0; i < Bt->B; ++i)
+    if (reps[i].status != FCT_OK && worst == FCT_OK) worst = static_cast<fct_status>(reps[i].status);
+  if (worst != FCT_OK) return fail(worst, std::string("solver finished with ") + fct_status_string(worst));
+  return FCT_OK;
+}
+
+fct_status fct_batch_destroy(fct_batch Bt) {
+  if (!Bt) return FCT_OK;
+  cudaDeviceSynchronize();
+  if (Bt->djobs) cudaFree(Bt->djobs);
+  if (Bt->ls) cudaFree(Bt->ls);
+  delete Bt;
   return FCT_OK;
 }
 

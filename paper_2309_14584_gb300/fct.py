@@ -122,6 +122,10 @@ SIGNATURES = [
     ("fct_execute", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_host", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_batch", ctypes.c_int, [ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P]),
+    ("fct_batch_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P, _P, _P, ctypes.c_int]),
+    ("fct_batch_launch", ctypes.c_int, [_P, _P]),
+    ("fct_batch_reports", ctypes.c_int, [_P, _P, _P]),
+    ("fct_batch_destroy", ctypes.c_int, [_P]),
     ("fct_plan_last_report", ctypes.c_int, [_P, _P, ctypes.POINTER(fct_report)]),
     ("fct_execute_noalloc", ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(fct_report)]),
     ("fct_destroy", ctypes.c_int, [_P]),
@@ -293,6 +297,35 @@ def fct_execute_batch(plans, samples, coeffs, team_blocks: int = 0, stream=None,
         return [r.as_dict() for r in reps]
     _check(lib().fct_execute_batch(B, hp, hs, hc, team_blocks, _stream(stream), None))
     return None
+
+
+def fct_batch_create(plans, samples, coeffs, team_blocks: int = 0) -> int:
+    """A prepared batch (include/fct.h): the job table stays on the device, so
+    fct_batch_launch needs nothing from the host and can be captured in a
+    CUDA graph."""
+    B = len(plans)
+    hp = (_P * B)(*plans)
+    hs = (_P * B)(*[_ptr(s) for s in samples])
+    hc = (_P * B)(*[_ptr(c) for c in coeffs])
+    out = _P()
+    _check(lib().fct_batch_create(ctypes.byref(out), B, hp, hs, hc, team_blocks))
+    return out.value
+
+
+def fct_batch_launch(batch: int, stream=None):
+    _check(lib().fct_batch_launch(batch, _stream(stream)))
+
+
+def fct_batch_reports(batch: int, n: int, stream=None) -> list:
+    reps = (fct_report * n)()
+    st = lib().fct_batch_reports(batch, _stream(stream), reps)
+    if st != FCT_OK:
+        raise FctError(st, lib().fct_last_error().decode())
+    return [r.as_dict() for r in reps]
+
+
+def fct_batch_destroy(batch: int):
+    _check(lib().fct_batch_destroy(batch))
 
 
 def fct_execute_noalloc(plan: int, samples, coeffs, stream=None, report: bool = True) -> dict | None:
