@@ -8,8 +8,10 @@ current stream; all arithmetic runs in libfct_gb300.so.
 
 Dimensions:
   * single transforms (autotune): block size, threads per coefficient in the
-    A^T q gather, entries per lane of the A p gather, and whether the grids
-    with long axes take their DCT passes on the tensor cores;
+    A^T q gather, entries per lane of the A p gather; then the A^T q gather
+    layout, the inner solve on the stored normal matrix (one team barrier per
+    iteration) and whether the grids with long axes take their DCT passes on
+    the tensor cores;
   * batches and serving (autotune_team_blocks): blocks per team.
 """
 from __future__ import annotations
@@ -44,34 +46,59 @@ def _time(fn, reps: int) -> float:
 
 
 def autotune(support, sizes, nodes, samples, options: dict, candidates=CANDIDATES, reps: int = 10) -> dict:
-    """Returns {"options": fastest options (options updated with a candidate),
-    "ms": its mean time, "timings": [(candidate, ms) for each candidate that
-    converged]}.  samples: device double[M] of this L-grid.  When the plan has
-    grids whose DCT runs on the tensor cores, every candidate is also timed
-    with those passes on the FP64 units (tensor_dct = -1)."""
+    """Returns {"options": fastest options (options updated with a candidate
+    and the toggles that won), "ms": its mean time, "timings": [(options
+    tried beyond `options`, ms) for each trial that converged]}.  samples:
+    device double[M] of this L-grid.
+
+    First the launch shapes of `candidates`; then, on the fastest shape, each
+    algorithmic choice the caller left open, flipped one at a time and kept
+    when faster: the A^T q gather layout (coef_split), for the mixed path the
+    inner solve on the stored W = A^T A (normal_matrix: one team barrier per
+    iteration, more entries), and for plans with tensor-core grids their DCT
+    on the FP64 units (tensor_dct = -1).  Choices a plan cannot take (W too
+    large) are skipped."""
     import torch
 
-    cands = [dict(c) for c in candidates]
-    probe = F.Plan(support, sizes, nodes, **options)
-    has_tc = probe.info.get("tensor_dct_grids", 0) > 0
-    probe.close()
-    if has_tc and "tensor_dct" not in options:
-        cands += [dict(c, tensor_dct=-1) for c in candidates]
     timings = []
-    for cand in cands:
-        opts = dict(options, **cand)
-        plan = F.Plan(support, sizes, nodes, **opts)
+
+    def measure(extra):
+        try:
+            plan = F.Plan(support, sizes, nodes, **dict(options, **extra))
+        except F.FctError:
+            return None, None
         try:
             c = torch.empty(plan.N, dtype=torch.float64, device=samples.device)
             if plan.execute(samples, c)["status"] != 0:
-                continue
-            timings.append((cand, _time(lambda: plan.execute(samples, c, report=False), reps)))
+                return None, None
+            ms = _time(lambda: plan.execute(samples, c, report=False), reps)
+            info = dict(plan.info)
+        except F.FctError:
+            return None, None
         finally:
             plan.close()
-    if not timings:
+        timings.append((dict(extra), ms))
+        return ms, info
+
+    best, best_ms, best_info = None, None, None
+    for cand in candidates:
+        ms, info = measure(dict(cand))
+        if ms is not None and (best_ms is None or ms < best_ms):
+            best, best_ms, best_info = dict(cand), ms, info
+    if best is None:
         raise RuntimeError("no launch shape converged")
-    cand, ms = min(timings, key=lambda t: t[1])
-    return {"options": dict(options, **cand), "ms": ms, "timings": timings}
+    toggles = []
+    if "coef_split" not in options:
+        toggles.append(dict(coef_split=-1 if best_info.get("coef_split") else 1))
+    if options.get("precision") == F.FCT_MIXED and "normal_matrix" not in options:
+        toggles.append(dict(normal_matrix=-1 if best_info.get("normal_nnz") else 1))
+    if "tensor_dct" not in options and best_info.get("tensor_dct_grids", 0) > 0:
+        toggles.append(dict(tensor_dct=-1))
+    for t in toggles:
+        ms, _ = measure(dict(best, **t))
+        if ms is not None and ms < best_ms:
+            best, best_ms = dict(best, **t), ms
+    return {"options": dict(options, **best), "ms": best_ms, "timings": timings}
 
 
 def autotune_team_blocks(handles, samples, coeffs, candidates=TEAM_BLOCKS, reps: int = 3) -> dict:

@@ -19,9 +19,13 @@ def test_autotune_choice_solves_to_tolerance():
     x = torch.from_numpy(f).cuda()
     opts = dict(precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)
     r = autotune(w.support, w.sizes, w.nodes, x, opts, reps=3)
-    assert len(r["timings"]) == len(CANDIDATES) and r["ms"] > 0
+    assert len(r["timings"]) >= len(CANDIDATES) and r["ms"] > 0
     chosen = {k: v for k, v in r["options"].items() if k not in opts}
-    assert chosen in [dict(c) for c in CANDIDATES]
+    shape = {k: v for k, v in chosen.items() if k not in ("coef_split", "normal_matrix", "tensor_dct")}
+    assert shape in [dict(c) for c in CANDIDATES]
+    tried = [t for t, _ in r["timings"]]
+    assert any("coef_split" in t for t in tried) and any("normal_matrix" in t for t in tried)
+    assert r["ms"] == min(ms for _, ms in r["timings"])
     plan = F.Plan(w.support, w.sizes, w.nodes, **r["options"])
     c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
     rep = plan.execute(x, c)
