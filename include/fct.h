@@ -53,7 +53,7 @@ extern "C" {
 typedef enum {
   FCT_OK = 0,
   FCT_ERR_INVALID_ARG = 1,  /* malformed sizes, support, options or pointers   */
-  FCT_ERR_RANK = 2,         /* reserved: plan rejected by a rank check          */
+  FCT_ERR_RANK = 2,         /* plan rejected by its rank check (kappa_max)      */
   FCT_ERR_NOCONV = 3,       /* iteration cap reached; best iterate is written   */
   FCT_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired               */
   FCT_ERR_OOM = 5,          /* device allocation failed                          */
@@ -133,6 +133,11 @@ typedef struct {
                          -1 = lane-split: coef_lanes threads of one warp per
                          coefficient.  Both give results independent of the team
                          size; they differ from each other by rounding order only. */
+  double kappa_max;   /* > 0: rank check (Algorithm 2's acceptance test, Sec. 3.3):
+                         fct_plan_create estimates kappa(A) by 200 Lanczos steps of
+                         fct_plan_condition from a fixed pseudo-random start and fails
+                         with FCT_ERR_RANK when the estimate exceeds kappa_max or A
+                         is rank-deficient.  0 (default) = no check.              */
 } fct_options;
 
 #define FCT_PLAN_BUILD_AUTO 0
@@ -172,6 +177,7 @@ typedef struct {
   int64_t tensor_dct_flops; /* BF16 tensor-core flops of the DCT passes per fct_execute
                                (36 digit-slice products of M 128 x N 64 x K 16 per tile
                                and K step); 0 without tensor-core grids              */
+  double kappa_estimate;    /* the rank check's kappa(A) estimate (0 without the check) */
 } fct_plan_info;
 
 /* Fill *opt with defaults: FP64, tol 1e-13, max_iter 50000, inner_tol 1e-6,
@@ -410,8 +416,7 @@ fct_status fct_selftest_wait_timeout(double timeout_s, int* status_out, double* 
  * eigenvalues.  *lambda_min, *lambda_max estimate sigma_min^2 and
  * sigma_max^2 of A from inside; *kappa = sqrt(lambda_max / lambda_min) is a
  * lower bound on kappa(A) that tightens as iterations grow (the CG
- * coefficients carry FP32-reduced norms, so the estimate resolves kappa up to
- * about 1e3); *used = iterations recorded (fewer when the iteration breaks
+ * coefficients come from FP64 inner products); *used = iterations recorded (fewer when the iteration breaks
  * down or the normal residual has fallen by 1e12, by which point the extreme
  * Ritz values have converged).  Outputs other than kappa may be NULL.
  * Synchronous.

@@ -286,6 +286,7 @@ struct fct_plan_s {
   bool stage_values = false;                // single launches stage the CG loop's entry values too
   int kernel_kind = 0;                      // solver kernel variant of single launches (kKernel*)
   int entries_per_lane = 0;                 // A p gather: entries per lane of a row unit
+  double kappa_est = 0.0;                   // rank check's kappa(A) estimate (0: not checked)
   double* d_stage_rhs_x = nullptr;          // fct_plan_rhs: scratch iterate of the first stage
   bool dirty_state = false;
   // DCT passes on the tensor cores (grids with a long axis; null when none):
@@ -498,6 +499,33 @@ unsigned long long timeout_ns(fct_plan P) {
 
 extern "C" {
 
+// Condition estimate of a finished plan for its rank check: kRankCheckIterations
+// Lanczos steps of fct_plan_condition from a fixed pseudo-random start
+// (splitmix64 of the index, uniform in [-1, 1)); scratch is taken and
+// returned on the plan's build stream.
+constexpr int kRankCheckIterations = 200;
+static fct_status rank_check(fct_plan P, cudaStream_t cs, double* kappa, double* lmin) {
+  const int64_t N = P->N;
+  std::vector<double> h(static_cast<size_t>(N));
+  for (int64_t i = 0; i < N; ++i) {
+    uint64_t z = static_cast<uint64_t>(i) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    h[static_cast<size_t>(i)] = static_cast<double>(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+  double* d = nullptr;
+  FCT_CUDA(cudaMallocAsync(&d, sizeof(double) * 2 * N, cs));
+  cudaError_t e = cudaMemcpyAsync(d, h.data(), sizeof(double) * N, cudaMemcpyHostToDevice, cs);
+  fct_status s = e == cudaSuccess ? FCT_OK : cuda_fail(e, "rank check upload");
+  int used = 0;
+  if (s == FCT_OK) s = fct_plan_condition(P, d, d + N, kRankCheckIterations, kappa, lmin, nullptr, &used, cs);
+  cudaFreeAsync(d, cs);
+  e = cudaStreamSynchronize(cs);
+  if (s == FCT_OK && e != cudaSuccess) s = cuda_fail(e, "rank check");
+  return s;
+}
+
 fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* support, int K, const int32_t* sizes,
                            const double* nodes, const fct_options* opt) {
   if (!out) return fail(FCT_ERR_INVALID_ARG, "out must not be NULL");
@@ -514,6 +542,7 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   if (o.coef_lanes != 0 && (o.coef_lanes < 1 || o.coef_lanes > 16 || (o.coef_lanes & (o.coef_lanes - 1))))
     return fail(FCT_ERR_INVALID_ARG, "coef_lanes must be 0 or a power of two <= 16");
   if (o.coef_split < -1 || o.coef_split > 1) return fail(FCT_ERR_INVALID_ARG, "coef_split must be -1, 0 or 1");
+  if (!(o.kappa_max >= 0.0)) return fail(FCT_ERR_INVALID_ARG, "kappa_max must be >= 0 (0 = no rank check)");
   if (o.entries_per_lane != 0 && o.entries_per_lane != 2 && o.entries_per_lane != 4 && o.entries_per_lane != 8)
     return fail(FCT_ERR_INVALID_ARG, "entries_per_lane must be 0, 2, 4 or 8");
   int ndev = 0;
@@ -869,6 +898,23 @@ fct_status fct_plan_create(fct_plan* out, int D, int64_t N, const uint16_t* supp
   H.wcsr.clear(); H.wcsr.shrink_to_fit();
   H.weight.clear(); H.weight.shrink_to_fit();
   H.crow.clear(); H.crow.shrink_to_fit();
+  if (o.kappa_max > 0.0) {
+    // Algorithm 2's acceptance test on the finished plan: refuse it when the
+    // Lanczos estimate of kappa(A) exceeds the bound (a rank-deficient A has
+    // a zero Ritz value, so its estimate is unbounded)
+    double kappa = 0.0, lmin = 0.0;
+    s = rank_check(P, cs, &kappa, &lmin);
+    if (s != FCT_OK) {
+      fct_destroy(P);
+      return s;
+    }
+    if (!(lmin > 0.0) || !(kappa <= o.kappa_max)) {
+      fct_destroy(P);
+      return fail(FCT_ERR_RANK, "kappa(A) estimate " + std::to_string(kappa) + " exceeds kappa_max " +
+                                    std::to_string(o.kappa_max) + " (or A is rank-deficient)");
+    }
+    P->kappa_est = kappa;
+  }
   *out = P;
   return FCT_OK;
 }
@@ -911,6 +957,7 @@ fct_status fct_plan_get_info(fct_plan P, fct_plan_info* info) {
   info->wide_rows = P->hp.n_wide_units;
   info->coef_chunks = P->hp.n_coef_chunks;
   info->entries_per_lane = P->entries_per_lane;
+  info->kappa_estimate = P->kappa_est;
   info->kernel_variant = P->kernel_kind;
   info->tensor_dct_grids = 0;
   info->tensor_dct_flops = 0;

@@ -55,6 +55,7 @@ class fct_options(ctypes.Structure):
         ("plan_build", ctypes.c_int),
         ("tensor_dct", ctypes.c_int),
         ("coef_split", ctypes.c_int),
+        ("kappa_max", ctypes.c_double),
     ]
 
 
@@ -94,6 +95,7 @@ class fct_plan_info(ctypes.Structure):
         ("entries_per_lane", ctypes.c_int32),
         ("kernel_variant", ctypes.c_int32),
         ("tensor_dct_flops", ctypes.c_int64),
+        ("kappa_estimate", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -107,3 +107,35 @@ def test_condition_estimate_past_convergence_stays_exact():
     r = lgrid.probe_condition(sup, sizes, nodes, iterations=400)
     assert r["iterations"] < 400
     assert r["kappa"] == pytest.approx(sv[0] / sv[-1], rel=1e-3)
+
+
+def test_rank_check_refuses_a_rank_deficient_plan():
+    """fct_options.kappa_max: the plan of the rank-deficient L-grid above (all
+    grids share the single-point node x = 1) is refused with FCT_ERR_RANK; the
+    same support on grids that separate it is accepted, with an estimate that
+    agrees with the oracle's exact kappa."""
+    D, d = 2, 3
+    sup = W.total_degree_support(D, d)
+    sizes = np.array([[1, 5], [1, 4], [1, 6]], dtype=np.int32)
+    with pytest.raises(F.FctError) as e:
+        F.Plan(sup, sizes, np.ones((3, D)), kappa_max=1e4)
+    assert e.value.status == F.fct.FCT_ERR_RANK
+    sup, sizes, nodes = _cands()
+    p = F.Plan(sup, sizes[:16], nodes[:16], kappa_max=1e4)
+    k = p.info["kappa_estimate"]
+    p.close()
+    exact = O.condition_number(O.AliasSystem(sup, sizes[:16], nodes[:16]).A)
+    assert 1.0 <= k <= exact * (1 + 1e-6) and k >= 0.9 * exact
+    p = F.Plan(sup, sizes[:16], nodes[:16])            # no check: no estimate
+    assert p.info["kappa_estimate"] == 0.0
+    p.close()
+    with pytest.raises(F.FctError) as e:                 # every kappa is >= 1
+        F.Plan(sup, sizes[:16], nodes[:16], kappa_max=0.5)
+    assert e.value.status == F.fct.FCT_ERR_RANK
+
+
+def test_rank_check_option_is_validated():
+    sup, sizes, nodes = _cands()
+    with pytest.raises(F.FctError) as e:
+        F.Plan(sup, sizes[:16], nodes[:16], kappa_max=-1.0)
+    assert e.value.status == F.fct.FCT_ERR_INVALID_ARG
