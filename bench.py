@@ -616,17 +616,21 @@ def run_gpu(args):
                        solver_blocks=info["grid_blocks"], block_threads=info["block_threads"],
                        coef_lanes=info["coef_lanes"], parallelism=f"replicas x{world}",
                        launch_tuning={"chosen": {k: v for k, v in R0["tuning"]["options"].items()
-                                                 if k in ("block_threads", "coef_lanes", "entries_per_lane")},
+                                                 if k in ("block_threads", "coef_lanes", "entries_per_lane",
+                                                          "coef_split", "normal_matrix", "tensor_dct")},
                                       "candidates_ms": [[c, round(ms, 4)] for c, ms in R0["tuning"]["timings"]]}),
         "rel_err_vs_oracle": R0["rel_err"],
-        "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"],
                      "traffic": profiled_traffic(HEADLINE_PROFILE) if best == "mixed" else None,
                      "kernel": "fct_solve_kernel", "algorithmic_bytes_per_launch": abytes,
-                     "peak_kind": "L2 read bandwidth measured live by fct_measure_l2 (32 MiB resident buffer)",
-                     "why_l2": "the CG loop's tables and vectors (about 23 MB) stay in the 129 MB L2; "
-                               "DRAM traffic per launch is the samples and DCT buffers",
-                     "hbm_peak": peaks["hbm_gbs"], "hbm_frac": achieved / peaks["hbm_gbs"],
-                     "hbm_peak_kind": f"{peak_kind} HBM copy bandwidth"},
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                     "note": "SURVEY 8(d) bytes per launch over the launch time; the CG loop's tables and "
+                             "vectors (about 23 MB) stay in the 129 MB L2, so DRAM traffic per launch is the "
+                             "samples and DCT buffers (traffic), and the loop is bound by scattered-load "
+                             "latency (gather_roofline) rather than by either bandwidth"},
+        "l2_roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                        "peak_kind": "L2 read bandwidth measured live by fct_measure_l2 (32 MiB resident buffer)"},
         "e2e": {"value": w.N / R0["e2e_s"], "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
                 "d2h_bytes_per_step": 8 * w.N + 32 + 4},
         "clocks": {k: R0["clocks"][k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
