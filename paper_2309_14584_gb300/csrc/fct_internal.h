@@ -30,12 +30,19 @@ constexpr int kLaneClasses = 7;
 //   out[e] = sum_j C[k][j] * in[e - k*stride + j*stride],  k = (e/stride) % n.
 struct DctChunk {
   int64_t base;            // grid's first sample in samples / y0 / y1
-  int32_t start, count;    // element range within the grid tensor
+  int32_t start, count;    // element range within the grid tensor (fibre range when fibres = 1)
   int32_t n, stride;       // axis length (1 = identity copy) and its stride
   int32_t mat;             // offset of the n x n matrix in dct_mats
   int8_t in_sel, out_sel;  // 0 = caller samples, 1 = y0, 2 = y1, 3 = caller samples (output)
-  int16_t pad;
+  int16_t fibres;          // 1: one thread per fibre computes all n outputs (even/odd split)
 };
+// Forward DCT passes of axes with kFibreMinN..kFibreMaxN points run one thread
+// per fibre, kFibreChunk fibres per work unit, when the pass has at least
+// kFibrePassMin fibres over all grids (several waves of GB300 threads).
+constexpr int kFibreMinN = 2;
+constexpr int kFibreMaxN = 16;
+constexpr int kFibreChunk = 512;
+constexpr int64_t kFibrePassMin = int64_t{1} << 18;
 static_assert(sizeof(DctChunk) == 32, "DctChunk layout");
 
 // Last DCT-I pass of a grid, evaluated only at its nonempty bins (fused with

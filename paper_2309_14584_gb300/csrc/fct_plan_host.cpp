@@ -351,6 +351,14 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
   H.npass = npass;
   H.pass_chunk_off.assign(1, 0);
   for (int p = 0; p < npass; ++p) {
+    // fibres of this pass over all grids: one thread per fibre pays only when
+    // they fill the GPU several times over (else one thread per output)
+    int64_t pass_fibres = 0;
+    for (int l = 0; l < K; ++l) {
+      const int A = static_cast<int>(active[l].size());
+      if (p >= A - 1) continue;
+      pass_fibres += (H.offsets[l + 1] - H.offsets[l]) / sizes[l * D + active[l][p]];
+    }
     for (int l = 0; l < K; ++l) {
       const int A = static_cast<int>(active[l].size());
       if (p >= A - 1) continue;
@@ -362,16 +370,22 @@ fct_status build_host_tables(int D, int64_t N, const uint16_t* support, int K,
       const int8_t out_sel = static_cast<int8_t>((p & 1) ? 2 : 1);
       const int8_t in_sel = p == 0 ? 0 : static_cast<int8_t>(((p - 1) & 1) ? 2 : 1);
       const int64_t T = H.offsets[l + 1] - H.offsets[l];
-      for (int64_t e0 = 0; e0 < T; e0 += kDctChunk) {
+      // short axes: units of fibres (one thread computes a fibre's n outputs);
+      // longer ones: units of output elements (one thread per output)
+      const bool by_fibre = n >= kFibreMinN && n <= kFibreMaxN && pass_fibres >= kFibrePassMin;
+      const int64_t units = by_fibre ? T / n : T;
+      const int64_t per = by_fibre ? kFibreChunk : kDctChunk;
+      for (int64_t e0 = 0; e0 < units; e0 += per) {
         DctChunk c{};
         c.base = H.offsets[l];
         c.start = static_cast<int32_t>(e0);
-        c.count = static_cast<int32_t>(std::min<int64_t>(kDctChunk, T - e0));
+        c.count = static_cast<int32_t>(std::min<int64_t>(per, units - e0));
         c.n = n;
         c.stride = static_cast<int32_t>(st);
         c.mat = mat;
         c.in_sel = in_sel;
         c.out_sel = out_sel;
+        c.fibres = by_fibre ? 1 : 0;
         H.dct_chunks.push_back(c);
       }
     }

@@ -162,8 +162,73 @@ __device__ void load_block_tabs(const DevPlan& P, const Team& tm, unsigned char*
 // ---------------------------------------------------------------------------
 // DCT-I: full axis pass over one work unit (all BT threads)
 // ---------------------------------------------------------------------------
+// One fibre x[0..N-1] (stride st) of an N-point axis to all N outputs, by the
+// symmetry of the DCT matrix: row k satisfies C[k][N-1-j] = (-1)^k C[k][j]
+// (DCT-I on extrema points and DCT-II on first-kind points alike), so even
+// rows need the pair sums x_j + x_{N-1-j} (plus the middle element when N is
+// odd; odd rows vanish there) and odd rows the pair differences: N loads,
+// N/2 additions and subtractions, about N^2/2 FMAs.
+template <int N>
+__device__ __forceinline__ void dct_fibre(const double* C, const double* in, double* out, int st, bool ro) {
+  constexpr int H = N / 2;
+  double x[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) x[j] = ro ? __ldg(in + j * st) : ldcg(in + j * st);
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const double a = x[j], b = x[N - 1 - j];
+    x[j] = a + b;          // pair sums at 0..H-1
+    x[N - 1 - j] = a - b;  // pair differences at N-H..N-1
+  }
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const double* Ck = C + k * N;
+    double acc = ((N & 1) && !(k & 1)) ? Ck[H] * x[H] : 0.0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) acc = fma(Ck[j], (k & 1) ? x[N - 1 - j] : x[j], acc);
+    stcg(out + k * st, acc);
+  }
+}
+
+// A work unit of fibres: fibre f = (p, q) of the (pre, n, post = stride) view
+// starts at element p n stride + q; consecutive threads take consecutive q.
+template <int BT>
+__device__ void dct_fibres(const DevPlan& P, const double* mats, const double* __restrict__ samples,
+                           const DctChunk& c) {
+  double* out = (c.out_sel == 1 ? P.y0 : P.y1) + c.base;
+  const double* in = (c.in_sel == 0 ? samples : (c.in_sel == 1 ? P.y0 : P.y1)) + c.base;
+  const double* C = mats + c.mat;
+  const bool ro = c.in_sel == 0;
+  const int st = c.stride;
+  for (int f = c.start + static_cast<int>(threadIdx.x); f < c.start + c.count; f += BT) {
+    const int p = f / st, q = f - p * st;
+    const int64_t b = static_cast<int64_t>(p) * c.n * st + q;
+    switch (c.n) {
+      case 2: dct_fibre<2>(C, in + b, out + b, st, ro); break;
+      case 3: dct_fibre<3>(C, in + b, out + b, st, ro); break;
+      case 4: dct_fibre<4>(C, in + b, out + b, st, ro); break;
+      case 5: dct_fibre<5>(C, in + b, out + b, st, ro); break;
+      case 6: dct_fibre<6>(C, in + b, out + b, st, ro); break;
+      case 7: dct_fibre<7>(C, in + b, out + b, st, ro); break;
+      case 8: dct_fibre<8>(C, in + b, out + b, st, ro); break;
+      case 9: dct_fibre<9>(C, in + b, out + b, st, ro); break;
+      case 10: dct_fibre<10>(C, in + b, out + b, st, ro); break;
+      case 11: dct_fibre<11>(C, in + b, out + b, st, ro); break;
+      case 12: dct_fibre<12>(C, in + b, out + b, st, ro); break;
+      case 13: dct_fibre<13>(C, in + b, out + b, st, ro); break;
+      case 14: dct_fibre<14>(C, in + b, out + b, st, ro); break;
+      case 15: dct_fibre<15>(C, in + b, out + b, st, ro); break;
+      default: dct_fibre<16>(C, in + b, out + b, st, ro); break;
+    }
+  }
+}
+
 template <int BT>
 __device__ void dct_unit(const DevPlan& P, const double* mats, const double* __restrict__ samples, const DctChunk& c) {
+  if (c.fibres) {
+    dct_fibres<BT>(P, mats, samples, c);
+    return;
+  }
   double* out = (c.out_sel == 1 ? P.y0 : P.y1) + c.base;
   const double* C = mats + c.mat;
   const int n = c.n, st = c.stride;
