@@ -376,3 +376,32 @@ def test_alias_operator_matches_oracle(case, kind):
     ref_aty = s.A.T @ y
     assert np.max(np.abs(ax.cpu().numpy()[order] - ref_ax)) <= 1e-13 * max(1.0, np.abs(ref_ax).max())
     assert np.max(np.abs(aty.cpu().numpy() - ref_aty)) <= 1e-13 * max(1.0, np.abs(ref_aty).max())
+
+
+@pytest.mark.parametrize("kind", ["extrema", "first"])
+def test_rhs_by_fibre_matches_oracle(kind):
+    """DCT passes with enough fibres run one thread per fibre with the even/odd
+    split of the DCT matrix rows: axes of 2..16 points (odd and even n), 2^18
+    or more fibres per pass; b must equal the oracle's direct DCT row by row."""
+    D, d, K = 4, 6, 400
+    sup = W.total_degree_support(D, d)
+    g = W.stream(77, "sizes")
+    sizes = g.integers(2, 17, size=(K, D)).astype(np.int32)
+    nodes = np.cos(np.pi * W.stream(77, "nodes").random((K, D)))
+    T = np.prod(sizes.astype(np.int64), axis=1)
+    for p in range(D - 1):   # every pass but the last runs by fibre
+        assert int(np.sum(T // sizes[:, p])) >= 1 << 18
+    params = W.gausscos_params(78, D)
+    f = O.sample_lgrid(W.FAMILY_GAUSSCOS, params, sup, sizes, nodes, kind=kind)
+    s = O.AliasSystem(sup, sizes, nodes, kind=kind)
+    ref = s.rhs(f)
+    gk = F.FCT_GRID_EXTREMA if kind == "extrema" else F.FCT_GRID_FIRST_KIND
+    plan = F.Plan(sup, sizes, nodes, grid_kind=gk, tensor_dct=-1)
+    b = torch.empty(plan.info["R"], dtype=torch.float64, device="cuda")
+    bins = F.fct_plan_rhs(plan.handle, torch.from_numpy(f).cuda(), b)
+    plan.close()
+    order = np.argsort(bins, kind="stable")
+    want_bins = np.concatenate([s.offsets[l] + s.rows[l] for l in range(len(s.rows))])
+    assert np.array_equal(bins[order], want_bins)
+    got = b.cpu().numpy()[order]
+    assert np.max(np.abs(got - ref)) <= 1e-13 * max(1.0, np.max(np.abs(f)))
