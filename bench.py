@@ -932,7 +932,19 @@ def run_batched(args, F, w, opts, flush) -> dict:
     for p in plans[1:]:
         p.close()
     base.close()
+    # the same batch on the plain FP64 path
+    base64 = F.Plan(w.support, w.sizes, w.nodes, **dict(PATH_OPTIONS["fp64"]))
+    plans = [base64] + [base64.clone() for _ in range(B - 1)]
+    hs = [p.handle for p in plans]
+    reps64 = F.fct_execute_batch(hs, xs, cs, team_blocks=tb)
+    ms64 = _timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), args.steps, flush)
+    for p in plans[1:]:
+        p.close()
+    base64.close()
+    fp64_path = {"value": B * w.N / (statistics.mean(ms64) / 1e3), "ms_per_launch": statistics.mean(ms64),
+                 "all_converged": all(r["status"] == 0 for r in reps64)}
     return {"workload": w.name, "transforms_per_launch": B, "team_blocks": tb,
+            "fp64_path": fp64_path, "mixed_over_fp64": (B * w.N / (statistics.mean(ms) / 1e3)) / fp64_path["value"],
             "graph": {"ms_per_launch": statistics.mean(gms), "value": B * w.N / (statistics.mean(gms) / 1e3),
                       "equals_direct_launch": gsame, "all_converged": gok,
                       "note": "fct_batch_launch captured into a CUDA graph, replayed"},
@@ -1002,6 +1014,20 @@ def run_hetero_batch(args, F, opts) -> dict:
            "team_blocks_tuning_ms": [[t, round(m, 1)] for t, m in tune["timings"]], "path": "mixed",
            "check_results": checks,
            "note": "inputs larger than L2; grid counts by Algorithm 2 (kappa0 = 20) before the timed region"}
+    for p in plans:
+        p.close()
+    # the same batch on the plain FP64 path (same L-grids, samples and team size)
+    fopts = dict(PATH_OPTIONS["fp64"])
+    with ThreadPoolExecutor(16) as ex:
+        plans = list(ex.map(lambda w: F.Plan(w.support, w.sizes, w.nodes, **fopts), ws))
+    hs = [p.handle for p in plans]
+    reps64 = F.fct_execute_batch(hs, xs, cs, team_blocks=tb)
+    ms64 = statistics.mean(_timed(lambda: F.fct_execute_batch(hs, xs, cs, team_blocks=tb, report=False), 2,
+                                  torch.empty(1, device="cuda")))
+    out["fp64_path"] = {"value": sum_n / (ms64 / 1e3), "ms_per_launch": ms64,
+                        "all_converged": all(r["status"] == 0 for r in reps64),
+                        "max_iterations": max(r["iterations"] for r in reps64)}
+    out["mixed_over_fp64"] = out["value"] / out["fp64_path"]["value"]
     for p in plans:
         p.close()
     return out
