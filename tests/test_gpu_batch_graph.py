@@ -95,3 +95,42 @@ def test_batch_create_rejects_bad_arguments():
         F.fct_batch_create(hs, [xs[0], 0], cs)           # a NULL buffer
     for p in plans:
         p.close()
+
+
+def test_graph_batch_of_grid_split_and_fp64_plans():
+    """A prepared batch mixing a grid-split plan (90 grids, wide rows) with FP64
+    and mixed plans of other shapes, replayed from a CUDA graph: each result
+    equals the transform alone bit for bit."""
+    sup = W.sparse_infinity_support(12, 30, 9, 2000, 3)
+    N, D = sup.shape
+    sizes, nodes = W.l_grid(130, N, D, 3 * D, 1, 10)
+    big = F.Plan(sup, sizes, nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)
+    assert big.info["coef_split"] == 1 and big.info["wide_rows"] > 0
+    ws, plans, xs, cs = _batch(3)
+    plans = list(plans)
+    fp = F.Plan(ws[0].support, ws[0].sizes, ws[0].nodes, precision=F.FCT_FP64, tol=1e-13)
+    xb = torch.empty(big.M, dtype=torch.float64, device="cuda")
+    big.sample(W.FAMILY_GAUSSCOS, W.gausscos_params(5, D), xb)
+    plans += [big, fp]
+    xs += [xb, xs[0]]
+    cs += [torch.full((big.N,), float("nan"), dtype=torch.float64, device="cuda"),
+           torch.full((fp.N,), float("nan"), dtype=torch.float64, device="cuda")]
+    b = F.fct_batch_create([p.handle for p in plans], xs, cs, team_blocks=16)
+    F.fct_batch_launch(b)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        F.fct_batch_launch(b)
+    for c in cs:
+        c.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(r["status"] == 0 for r in F.fct_batch_reports(b, len(plans)))
+    for p, x, c in zip(plans, xs, cs):
+        alone = torch.empty_like(c)
+        assert p.execute(x, alone)["status"] == 0
+        assert torch.equal(alone, c)
+    del g
+    F.fct_batch_destroy(b)
+    for p in plans:
+        p.close()
