@@ -846,9 +846,10 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
     if not large_sparse:
         return out
     # the paper's sparse-support scale: N = 1e6 multi-indices at D = 100 (10 nonzero
-    # components of degree <= 3 each), 400 grids by Algorithm 1; one transform, timed
-    # with CUDA events, the polynomial on the support recovered
-    D, d, N, K = 100, 3, 1_000_000, 400
+    # components of degree <= 3 each), 600 grids by Algorithm 1 (measured: 300 grids
+    # do not converge in 3000 inner iterations, 400 take 28 s, 600 take 21 s); one
+    # transform, timed with CUDA events, the polynomial on the support recovered
+    D, d, N, K = 100, 3, 1_000_000, 600
     sup = W.sparse_support_vectorised(3, D, d, N, 10)
     sizes, nodes = W.l_grid(500, N, D, K, 1, d + 1)
     c_true = W.poly_coefficients(10, sup)

@@ -88,10 +88,10 @@ def test_sparse_support_D100_large_exact_recovery():
 @pytest.mark.slow
 def test_sparse_support_D100_N1e6_exact_recovery():
     """The paper's sparse-support scale: 10^6 random multi-indices at D = 100
-    (10 nonzero components of degree <= 3 each), 400 grids by Algorithm 1
-    (K N = 4e8 table entries, M = 8.1e8 samples); a polynomial on that support
+    (10 nonzero components of degree <= 3 each), 600 grids by Algorithm 1
+    (K N = 6e8 table entries, M = 1.2e9 samples); a polynomial on that support
     is recovered by the mixed path (the check that holds at any size)."""
-    D, d, N, K = 100, 3, 1_000_000, 400
+    D, d, N, K = 100, 3, 1_000_000, 600
     sup = W.sparse_support_vectorised(3, D, d, N, 10)
     sizes, nodes = W.l_grid(500, N, D, K, 1, d + 1)
     c_true = W.poly_coefficients(10, sup)
