@@ -625,7 +625,8 @@ def run_gpu(args):
                      "traffic": profiled_traffic(HEADLINE_PROFILE) if best == "mixed" else None,
                      "kernel": "fct_solve_kernel", "algorithmic_bytes_per_launch": abytes,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
-                     "note": "SURVEY 8(d) bytes per launch over the launch time; the CG loop's tables and "
+                     "note": "algorithmic bytes per launch (table indices and vectors of every CG iteration and sweep, "
+                             "DCT samples and bins) over the launch time; the CG loop's tables and "
                              "vectors (about 23 MB) stay in the 129 MB L2, so DRAM traffic per launch is the "
                              "samples and DCT buffers (traffic), and the loop is bound by scattered-load "
                              "latency (gather_roofline) rather than by either bandwidth"},
