@@ -22,7 +22,7 @@ constexpr int kMaxAxis = 4096;         // longest grid axis (points) the direct 
 // every gather warp of a block (one row per unit), the warps' partial sums
 // added in warp order.
 constexpr int kWideLanes = 64;
-constexpr int kWideRowFactor = 4;
+constexpr int kWideRowFactor = 16;
 constexpr int kLaneClasses = 7;
 
 // One DCT-I work unit: a contiguous element range of one grid tensor in one

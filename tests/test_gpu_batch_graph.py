@@ -104,7 +104,7 @@ def test_graph_batch_of_grid_split_and_fp64_plans():
     sup = W.sparse_infinity_support(12, 30, 9, 2000, 3)
     N, D = sup.shape
     sizes, nodes = W.l_grid(130, N, D, 3 * D, 1, 10)
-    big = F.Plan(sup, sizes, nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4)
+    big = F.Plan(sup, sizes, nodes, precision=F.FCT_MIXED, tol=1e-12, inner_tol=1e-4, entries_per_lane=2)
     assert big.info["coef_split"] == 1 and big.info["wide_rows"] > 0
     ws, plans, xs, cs = _batch(3)
     plans = list(plans)

@@ -109,10 +109,11 @@ def test_sparse_support_D100_N1e6_exact_recovery():
 @pytest.mark.parametrize("bt", [128, 256, 512])
 def test_wide_rows_match_oracle_and_batch(bt):
     """Sparse supports put most columns in bin 0 of a grid: rows of more than
-    4 x 32 x 8 entries are gathered by every warp of a block (the warps'
-    partial sums added in a fixed order).  The plan must hold such rows, the
-    FP64 and mixed solves match the oracle, and a batch on small teams gives
-    the coefficients of the transform alone bit for bit."""
+    16 x 32 x (entries per lane) entries are gathered by every warp of a block
+    (the warps' partial sums added in a fixed order); 2 entries per lane put
+    this plan's ~1.5k-entry rows above that.  The plan must hold such rows,
+    the FP64 and mixed solves match the oracle, and a batch on small teams
+    gives the coefficients of the transform alone bit for bit."""
     sup = W.sparse_infinity_support(12, 30, 9, 2000, 3)
     N, D = sup.shape
     sizes, nodes = W.l_grid(130, N, D, 3 * D, 1, 10)
@@ -122,9 +123,9 @@ def test_wide_rows_match_oracle_and_batch(bt):
     x = torch.from_numpy(f).cuda()
     for opts, tol in ((dict(precision=F.FCT_FP64, tol=1e-14), 1e-11),
                       (dict(precision=F.FCT_MIXED, tol=1e-13, inner_tol=1e-5), 1e-10)):
-        plan = F.Plan(sup, sizes, nodes, block_threads=bt, **opts)
+        plan = F.Plan(sup, sizes, nodes, block_threads=bt, entries_per_lane=2, **opts)
         lens = np.diff(F.fct_plan_tables(plan.handle)["rowptr"])
-        assert lens.max() > 4 * 32 * 8
+        assert lens.max() > 16 * 32 * 2 and plan.info["wide_rows"] > 0
         c = torch.full((N,), float("nan"), dtype=torch.float64, device="cuda")
         rep = plan.execute(x, c)
         assert rep["status"] == 0, rep
