@@ -25,6 +25,32 @@ constexpr int kWideLanes = 64;
 constexpr int kWideRowFactor = 16;
 constexpr int kLaneClasses = 7;
 
+// Solver row order: ascending key = (class number, 6 - log2(lanes): wide rows
+// first, then 32 lanes, ..., 1 lane) above 16 bits that are zero unless the
+// plan has at least kRoundsOrderMinEntries table entries (K N); there they
+// hold 65535 - load rounds, the rounds being ceil(len / (32 * epl)) capped at
+// 65535.  Rows of fewer than 32 lanes take one round by construction, so only
+// 32-lane and wide rows move: longest first, so that the rows a block's warps
+// take side by side between two block barriers need about as many rounds.
+// Smaller plans keep the class order alone: their blocks stage their units in
+// shared memory in unit order, and a block whose first unit holds all the
+// longest rows would stage fewer of its units than the others.  Both row
+// builders sort stably by this key (equal keys keep ascending bin order).
+// lanes = lanes_for(len, epl).
+constexpr int64_t kRoundsOrderMinEntries = int64_t(1) << 23;
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int32_t row_order_key(int64_t len, int lanes, int epl, bool by_rounds) {
+  int cls = 0;
+  while ((1 << cls) < lanes) ++cls;
+  const int64_t per = 32 * static_cast<int64_t>(epl);
+  int64_t rounds = (len + per - 1) / per;
+  if (rounds > 65535) rounds = 65535;
+  return static_cast<int32_t>(((kLaneClasses - 1 - cls) << 16) | (by_rounds ? 65535 - rounds : 0));
+}
+constexpr int kRowOrderKeyBits = 19;  // class (3 bits) above 16 bits of rounds
+
 // One DCT-I work unit: a contiguous element range of one grid tensor in one
 // axis pass.  Output element e (within the grid) is
 //   out[e] = sum_j C[k][j] * in[e - k*stride + j*stride],  k = (e/stride) % n.
@@ -354,10 +380,10 @@ int pick_entries_per_lane(const int64_t classes[3][kLaneClasses], int workers, i
 // kWideRowFactor * 32 * epl.
 int lanes_for(int32_t len, int epl);
 
-// Renumber the rows of H for the device: stable sort by descending gather
-// lane count, so that rows with equal lane counts are contiguous and keep
-// their ascending-bin order.  Rewrites rowptr, col, wcsr, rowsrc, rowgrid and
-// crow in place.
+// Renumber the rows of H for the device: stable sort by row_order_key
+// (descending gather lane count, then descending load rounds), so that rows
+// with equal lane counts are contiguous; equal keys keep their ascending-bin
+// order.  Rewrites rowptr, col, wcsr, rowsrc, rowgrid and crow in place.
 void device_row_order(HostTables* H, int epl);
 
 // A p gather units for `workers` threads per block: a unit holds

@@ -14,8 +14,9 @@
 //   3. compaction: a row starts where the key changes (flags, exclusive
 //      scan) -> rowptr, the row's sample index and grid, columns, values and
 //      the coefficient-major row table;
-//   4. the device row order: one more stable radix pass over the rows, keyed
-//      by the gather lane class (most lanes first), then the entries and the
+//   4. the device row order: a stable radix sort of the rows, keyed by the
+//      gather lane class (most lanes first) and, for 32-lane and wide rows of
+//      large plans, the load rounds (most first), then the entries and the
 //      row table are permuted to it.
 // Everything between the upload of the support and the download of the row
 // pointers runs on the device; the host only chooses the entries per lane
@@ -351,12 +352,15 @@ __global__ void lane_class_kernel(const int32_t* __restrict__ rowptr, int64_t R,
   if (threadIdx.x < kClassCounters) atomicAdd(&hist[threadIdx.x], h[threadIdx.x]);
 }
 
-// Row sort key: 6 - log2(lanes), so wide rows come first, then 32 lanes, ...
-__global__ void row_class_key_kernel(const int32_t* __restrict__ rowptr, int64_t R, int epl,
+// Row sort key (row_order_key): wide rows first, then 32 lanes, ...; with
+// by_rounds, inside the 32-lane and wide classes the rows with more load
+// rounds first.
+__global__ void row_class_key_kernel(const int32_t* __restrict__ rowptr, int64_t R, int epl, bool by_rounds,
                                      int32_t* __restrict__ key, int32_t* __restrict__ val) {
   for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < R;
        r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    key[r] = (kLaneClasses - 1) - (__ffs(lanes_for_dev(rowptr[r + 1] - rowptr[r], epl)) - 1);
+    const int32_t len = rowptr[r + 1] - rowptr[r];
+    key[r] = row_order_key(len, lanes_for_dev(len, epl), epl, by_rounds);
     val[r] = static_cast<int32_t>(r);
   }
 }
@@ -619,11 +623,12 @@ fct_status build_device_tables(HostTables* Hp, const uint16_t* support, const in
   const int epl = pick_entries_per_lane(classes, workers, wave, fixed_epl);
   *epl_out = epl;
 
-  // 4. device row order: one stable pass keyed by the lane class (reuses
-  // the sort buffers: the sorted pairs are no longer needed)
+  // 4. device row order: a stable sort keyed by row_order_key (reuses the
+  // sort buffers: the sorted pairs are no longer needed)
   int32_t *rk = d_k0, *rv = d_v0, *rk2 = d_k1, *rv2 = d_v1;
-  row_class_key_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(d_rowptr0, R, epl, rk, rv);
-  radix_sort(&rk, &rv, &rk2, &rv2, R, 3, d_ghist, d_part, d_small, st);
+  row_class_key_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(d_rowptr0, R, epl, KN >= kRoundsOrderMinEntries, rk,
+                                                                 rv);
+  radix_sort(&rk, &rv, &rk2, &rv2, R, kRowOrderKeyBits, d_ghist, d_part, d_small, st);
   const int32_t* order = rv;
   row_perm_kernel<<<elem_blocks(R), kElemThreads, 0, st>>>(order, R, d_rowptr0, d_rowsrc0, d_rowgrid0, out->rowptr, d_inv,
                                                     d_rowsrc, out->rowgrid);

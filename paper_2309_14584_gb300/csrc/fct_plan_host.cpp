@@ -399,11 +399,16 @@ void device_row_order(HostTables* Hp, int epl) {
   const int64_t R = H.R;
   std::vector<int32_t> order(R);
   for (int64_t r = 0; r < R; ++r) order[r] = static_cast<int32_t>(r);
-  // stable sort by gather lane class only: rows keep their bin order within a
-  // class, which keeps neighbouring coefficients' rows close together
-  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-    return lanes_for(H.rowptr[a + 1] - H.rowptr[a], epl) > lanes_for(H.rowptr[b + 1] - H.rowptr[b], epl);
-  });
+  // stable sort by row_order_key: gather lane class, then (32-lane and wide
+  // rows of large plans) load rounds, longest first; equal keys keep their
+  // bin order, which keeps neighbouring coefficients' rows close together
+  const bool by_rounds = static_cast<int64_t>(H.K) * H.N >= kRoundsOrderMinEntries;
+  std::vector<int32_t> key(R);
+  for (int64_t r = 0; r < R; ++r) {
+    const int32_t len = H.rowptr[r + 1] - H.rowptr[r];
+    key[r] = row_order_key(len, lanes_for(len, epl), epl, by_rounds);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
   std::vector<int32_t> inv(R), rowptr(R + 1), col(H.col.size()), rowsrc(R), rowgrid(R);
   std::vector<double> wcsr(H.wcsr.size());
   rowptr[0] = 0;

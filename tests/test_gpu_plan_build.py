@@ -29,6 +29,14 @@ def _sparse(seed, D, d, N, kpd):
     return sup, sizes, nodes
 
 
+def _sparse10(N, K):
+    """D = 100, 10 nonzero components of degree <= 3: rows of every length from
+    1 to thousands of entries (32-lane rows of several load rounds)."""
+    sup = W.sparse_support_vectorised(3, 100, 3, N, 10)
+    sizes, nodes = W.l_grid(500, N, 100, K, 1, 4)
+    return sup, sizes, nodes
+
+
 # name, (support, sizes, nodes) maker, plan options.  Sizes span one radix
 # tile (K N < 4096) to K N = 6e6 (several hundred tiles, three 8-bit passes),
 # single-point axes, both grid kinds, the three block sizes (different entries
@@ -44,6 +52,8 @@ CASES = [
     ("d10", lambda: _wl(W.config_d10_rational()), {}),
     ("sinf_d30", lambda: _sparse(12, 30, 9, 2000, 3), {}),
     ("sinf_d100", lambda: _sparse(13, 100, 6, 20000, 3), {}),
+    ("sinf_d100_nz10", lambda: _sparse10(20000, 60), {}),
+    ("sinf_d100_nz10_rounds", lambda: _sparse10(40000, 220), {}),
 ]
 
 
@@ -145,3 +155,54 @@ def test_default_build_is_on_the_device_and_bad_value_is_rejected():
     w = W.config_small_poly()
     with pytest.raises(F.FctError):
         F.Plan(w.support, w.sizes, w.nodes, plan_build=3)
+
+
+def _lanes_for(length, epl):
+    lanes = 1
+    while lanes < 32 and lanes * epl < length:
+        lanes *= 2
+    return 64 if length > 16 * 32 * epl else lanes
+
+
+@pytest.mark.parametrize("epl", [2, 8])
+def test_solver_row_order_of_a_large_plan(epl):
+    """K N = 8.8e6 table entries (at least 2^23): rows in solver order have
+    non-increasing gather lanes (wide rows first); inside the 32-lane class
+    and among wide rows, non-increasing load rounds ceil(len / (32 epl)); rows
+    with equal lanes and rounds keep ascending bin order."""
+    sup, sizes, nodes = _sparse10(40000, 220)
+    assert sizes.shape[0] * sup.shape[0] >= 1 << 23
+    p = F.Plan(sup, sizes, nodes, entries_per_lane=epl)
+    try:
+        t = F.fct_plan_tables(p.handle)
+        assert p.info["entries_per_lane"] == epl
+    finally:
+        p.close()
+    lens = np.diff(t["rowptr"])
+    lanes = np.array([_lanes_for(int(n), epl) for n in lens])
+    rounds = -(-lens // (32 * epl))
+    assert np.all(np.diff(lanes) <= 0)
+    assert (lanes == 32).sum() > 1000 and len(np.unique(rounds[lanes == 32])) >= 5
+    same = lanes[1:] == lanes[:-1]
+    long_rows = same & (lanes[1:] >= 32)
+    assert np.all(np.diff(rounds)[long_rows] <= 0)
+    tie = same & ((lanes[1:] < 32) | (rounds[1:] == rounds[:-1]))
+    assert np.all(np.diff(t["bins"])[tie] > 0)
+
+
+def test_solver_row_order_of_a_small_plan():
+    """Below 2^23 table entries the rows keep ascending bin order inside each
+    lane class, whatever their load rounds."""
+    sup, sizes, nodes = _sparse10(20000, 60)
+    p = F.Plan(sup, sizes, nodes, entries_per_lane=2)
+    try:
+        t = F.fct_plan_tables(p.handle)
+    finally:
+        p.close()
+    lens = np.diff(t["rowptr"])
+    lanes = np.array([_lanes_for(int(n), 2) for n in lens])
+    assert np.all(np.diff(lanes) <= 0)
+    rounds = -(-lens // 64)
+    assert len(np.unique(rounds[lanes == 32])) >= 5
+    same = lanes[1:] == lanes[:-1]
+    assert np.all(np.diff(t["bins"])[same] > 0)
