@@ -539,7 +539,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and "mixed" in results and not args.no_next_rows:
         try:
             next_rows = run_next_rows(F, alt_workload(), dict(PATH_OPTIONS["mixed"]), flush,
-                                      large_sparse=not args.no_large_sparse)
+                                      large_sparse=not args.no_large_sparse,
+                                      gather_peak=roofs["l2"]["gather_gloads_per_s"])
         except Exception as e:  # measurement only; the bench line stands without it
             next_rows = {"error": str(e)[:200]}
 
@@ -757,7 +758,22 @@ def approximation_error(F, plan, w, coeffs_dev) -> dict:
             "note": "max |p(x) - f(x)| of the mixed-path expansion at uniform random points"}
 
 
-def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
+def sparse_rooflines(info, rep, ms, peaks, peak_kind, gather_peak):
+    """Roofs of a sparse-support transform, whose tables (K N entries, more
+    than L2 holds) are read from DRAM every iteration: the algorithmic bytes
+    against the measured HBM copy rate, and the scattered loads (one per table
+    entry and alias pass) against the measured random-gather rate."""
+    bytes_ = algorithmic_bytes(info, rep, "mixed")
+    hbm = {"bound": "hbm", "achieved": bytes_ / (ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "algorithmic_bytes_per_launch": bytes_,
+           "peak_kind": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json)",
+           "note": "table bytes counted as indices only (4 per entry and alias pass); the stored FP32 entry "
+                   "values double the table bytes actually read"}
+    hbm["frac"] = hbm["achieved"] / hbm["peak"]
+    return hbm, gather_roofline(info, rep, ms / 1e3, gather_peak)
+
+
+def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True, gather_peak=None) -> dict:
     """The rows past the hot path, timed on the same GPU: the paper's
     first-kind grid, evaluation of the expansion at random points, and
     sparse S^inf supports at D = 100 (N = 2e4, and N = 1e6 unless
@@ -842,6 +858,9 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
                           "plan_build_ms": 1e3 * t_build, "ms_per_transform": ms, "value": N / (ms / 1e3),
                           "unit": UNIT, "status": rep["status"], "iterations": rep["iterations"],
                           "refinements": rep["refinements"], "recovery_rel_err": err}
+    if gather_peak:
+        out["sparse_D100"]["roofline"], out["sparse_D100"]["gather_roofline"] = sparse_rooflines(
+            dict(ps.info), rep, ms, peaks, peak_kind, gather_peak)
     ps.close()
     del xs, cs
     if not large_sparse:
@@ -874,6 +893,9 @@ def run_next_rows(F, w, opts, flush, steps=20, large_sparse=True) -> dict:
                                "plan_build_ms": 1e3 * t_build, "ms_per_transform": ms, "value": N / (ms / 1e3),
                                "unit": UNIT, "status": rep["status"], "iterations": rep["iterations"],
                                "refinements": rep["refinements"], "recovery_rel_err": err}
+    if gather_peak:
+        out["sparse_D100_N1e6"]["roofline"], out["sparse_D100_N1e6"]["gather_roofline"] = sparse_rooflines(
+            dict(pl.info), rep, ms, peaks, peak_kind, gather_peak)
     pl.close()
     return out
 
