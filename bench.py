@@ -66,6 +66,7 @@ PROFILE_CASES = {
     "d6_mixed": ("config_d6_gausscos", "mixed", {}),
     "d2_tensor_dct": ("tc_profile_workload", "mixed", {}),
     "sparse_d100": ("sparse_profile_workload", "mixed", {"block_threads": 512}),
+    "sparse10_d100": ("sparse10_profile_workload", "mixed", {"block_threads": 512}),
 }
 
 
@@ -1274,6 +1275,18 @@ def sparse_profile_workload():
     sizes, nodes = W.l_grid(300, N, D, 10 * D, 1, d + 1)
     c = W.poly_coefficients(10, sup)
     return W.Workload("sparse_D100_N2e4_K1000", D, d, sup, sizes, nodes, W.FAMILY_POLY, c, c, 1e-12, "mixed")
+
+
+def sparse10_profile_workload():
+    """Sparse S^inf support at D = 100 (N = 1e5, 10 nonzero components of degree
+    <= 3 per index), 240 grids, seeded polynomial target: rows of every length
+    from 1 to ~37k entries."""
+    import workloads as W
+    D, d, N, K = 100, 3, 100_000, 240
+    sup = W.sparse_support_vectorised(3, D, d, N, 10)
+    sizes, nodes = W.l_grid(500, N, D, K, 1, d + 1)
+    c = W.poly_coefficients(10, sup)
+    return W.Workload("sparse10_D100_N1e5_K240", D, d, sup, sizes, nodes, W.FAMILY_POLY, c, c, 1e-12, "mixed")
 
 
 def run_profile(args):
